@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark: transpose + sum reduction at roofline scale on GB300.
+
+One step = one out-of-place transpose of a 16384x16384 float32 matrix plus
+one sum of a 2^28-element float32 vector (both N(0,1), seed 1), i.e. the whole
+hot path once over one batch of synthetic input.  Inputs (1 GiB each) are far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+value   = algorithmic bytes per step / device time per step, in GB/s, with the
+          inputs resident in HBM (2*N*4 bytes for the transpose, N*4 for the
+          sum: the thesis's effective-bandwidth convention (R_B + W_B) / t,
+          Sec. 7.1), summed over all ranks / max over ranks of the time.
+e2e     = the same metric through the public API with host buffers: the
+          pinned host inputs are copied in and the results copied out inside
+          the timed region.
+roofline: the dominant kernel (the transpose), its achieved GB/s from CUDA
+          events on its launch stream against the measured HBM copy peak.
+cpu_baseline: the CPU oracle timed on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle (the only reference implementation
+of this path) on the host cores instead, on the same metric and config.
+Multi-GPU (torchrun): replicas only -- every rank runs its own copy of the
+step on its own GPU; there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ROWS = COLS = 16384
+N_SUM = 1 << 28
+ESIZE = 4
+T_BYTES = 2 * ROWS * COLS * ESIZE   # transpose: read + write
+R_BYTES = N_SUM * ESIZE             # sum: read
+STEP_BYTES = T_BYTES + R_BYTES
+WORKLOAD = "transpose 16384x16384 fp32 + sum 2^28 fp32, N(0,1), seed 1"
+METRIC = "transpose/reduce HBM GB/s (% of GB300 peak)"
+
+# DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
+# ncu capture; kept only while the kernel source is unchanged (sha256 below).
+NCU_TRANSPOSE_TRAFFIC = {"bytes": None, "src_sha256": None}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_sha(name):
+    with open(os.path.join(ROOT, "paper_2605_13864_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """The CPU oracle on a bounded sample of the workload (single thread)."""
+    import oracle
+    from paper_2605_13864_gb300 import workloads
+
+    side, n = 4096, 1 << 24
+    mat = workloads.roofline_matrix(side, side)
+    vec = workloads.roofline_vector(n)
+    oracle.transpose(mat[:64, :64])
+    t_bytes = 2 * side * side * ESIZE
+    r_bytes = n * ESIZE
+    done_bytes, t0 = 0, time.perf_counter()
+    reps = 0
+    while True:
+        oracle.transpose(mat)
+        oracle.sum_f64(vec)
+        done_bytes += t_bytes + r_bytes
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done_bytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x (transpose 4096x4096 fp32 + sum 2^24 fp32) in {dt:.1f} s, "
+                      "plain C oracle, one host thread"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2605_13864_gb300 import workloads
+
+    side, n = 4096, 1 << 24
+    mat = workloads.roofline_matrix(side, side)
+    vec = workloads.roofline_vector(n)
+    step_bytes = 2 * side * side * ESIZE + n * ESIZE
+    for _ in range(args.warmup):
+        oracle.transpose(mat)
+        oracle.sum_f64(vec)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.transpose(mat)
+        oracle.sum_f64(vec)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = step_bytes * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "transpose 4096x4096 fp32 + sum 2^24 fp32 per step",
+                   "l2": "host run"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: transpose 4096x4096 fp32 + sum 2^24 fp32, one host thread"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2605_13864_gb300 import api, workloads
+    api.transpose(torch.zeros((64, 64), device="cuda"))  # load + warm the library
+
+    # Inputs resident in HBM before the timed region.
+    mat_h = workloads.roofline_matrix(ROWS, COLS)
+    vec_h = workloads.roofline_vector(N_SUM)
+    mat = torch.from_numpy(mat_h).cuda()
+    vec = torch.from_numpy(vec_h).cuda()
+    out_t = torch.empty((COLS, ROWS), dtype=torch.float32, device="cuda")
+    out_r = torch.empty((), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        api.transpose(mat, out=out_t)
+        api.reduce_sum(vec, out=out_r)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # Device-timed region: per-kernel events on the launch stream.
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        api.transpose(mat, out=out_t)
+        ev[k][1].record(stream)
+        api.reduce_sum(vec, out=out_r)
+        ev[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    t_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    r_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    api.stream_status()
+
+    # End to end through the public API with host buffers.
+    mat_p = torch.from_numpy(mat_h).pin_memory()
+    vec_p = torch.from_numpy(vec_h).pin_memory()
+    out_tp = torch.empty((COLS, ROWS), dtype=torch.float32).pin_memory()
+    del mat, vec, out_t
+    torch.cuda.empty_cache()
+    api.transpose(mat_p, out=out_tp)
+    api.reduce_sum(vec_p)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        api.transpose(mat_p, out=out_tp)
+        api.reduce_sum(vec_p).item()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    local_ms = total_ms / args.steps
+    if dist:
+        tt = torch.tensor([local_ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms, e2e_s = float(tt[0]), float(tt[1])
+    else:
+        step_ms = local_ms
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        value = world * STEP_BYTES / (step_ms * 1e-3) / 1e9
+        t_avg = statistics.mean(t_ms)
+        r_avg = statistics.mean(r_ms)
+        achieved = T_BYTES / (t_avg * 1e-3) / 1e9
+        traffic = NCU_TRANSPOSE_TRAFFIC["bytes"]
+        if traffic is not None and NCU_TRANSPOSE_TRAFFIC["src_sha256"] != _src_sha("transpose.cu"):
+            traffic = None
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(step_ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (1 GiB each), no flush",
+                       "peak_gbs": peak, "peak_kind": peak_kind},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "transpose_tma_kernel<4,64,64,4>", "peak_kind": peak_kind},
+            "components": {
+                "transpose_ms": round(t_avg, 4), "transpose_gbs": round(achieved, 1),
+                "transpose_frac_of_peak": round(achieved / peak, 4),
+                "transpose_frac_of_8tbs": round(achieved / 8000.0, 4),
+                "reduce_ms": round(r_avg, 4), "reduce_gbs": round(R_BYTES / (r_avg * 1e-3) / 1e9, 1),
+                "reduce_frac_of_peak": round(R_BYTES / (r_avg * 1e-3) / 1e9 / peak, 4),
+            },
+            "e2e": {"value": round(STEP_BYTES / e2e_s / 1e9 * world, 3), "unit": "GB/s",
+                    "h2d_bytes_per_step": ROWS * COLS * ESIZE + N_SUM * ESIZE,
+                    "d2h_bytes_per_step": ROWS * COLS * ESIZE + 8, "steps": e2e_steps},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["optigpu", "reference"], default="optigpu")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * optigpu.h -- C ABI of the GB300 (sm_103a) transpose and sum-reduction
+ * library.
+ *
+ * The two operations are the case studies of the thesis "Source-to-Source
+ * Transformations for GPU Code Generation" (arxiv 2605.13864):
+ *
+ *   transpose   Listing 3.5, Sec. 3.1:  out[x][y] = in[y][x]  for x < W, y < H.
+ *               Here H = rows, W = cols, `src` is rows x cols and `dst` is
+ *               cols x rows, both dense row-major, so
+ *               dst[c * rows + r] = src[r * cols + c].  The thesis's problem
+ *               is out-of-place (Listings 3.5, 3.11), so src and dst must not
+ *               overlap.  Elements are copied bit for bit.
+ *
+ *   reduce_sum  Listing 2.1, Sec. 2.1:  the result is reduce_sum(N, A), the
+ *               sum of A(0) .. A(N-1).  Listing 2.2 (Sec. 2.2.1) splits it
+ *               into per-chunk partial sums followed by a sum of the partials;
+ *               this library computes the partials on the GPU and finishes
+ *               them on the GPU too (the thesis's benchmark finishes them on
+ *               the host, Sec. 7.1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named src/dst/out are DEVICE pointers owned by the caller
+ *     (allocate them with cudaMalloc, torch, ...); the library never frees
+ *     them.  The library owns its internal workspaces.
+ *   - `stream` is a cudaStream_t passed as an opaque pointer (NULL = the
+ *     legacy default stream).  Calls are asynchronous: they validate the
+ *     arguments, enqueue kernels on `stream` and return without waiting.
+ *   - A call that returns anything but OPTIGPU_OK has enqueued nothing
+ *     (argument errors are found before any launch).  Errors raised while
+ *     the kernels run are reported by optigpu_stream_status().
+ *   - Calls are thread-safe.  Calls on one stream are ordered by the stream;
+ *     calls on different streams use different workspaces.
+ */
+#ifndef OPTIGPU_H
+#define OPTIGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OPTIGPU_VERSION 100 /* 1.0.0 */
+
+/* A cudaStream_t. */
+typedef void *optigpu_stream_t;
+
+/* Element types.  The transpose copies 4-byte (INT32, FLOAT32) or 2-byte
+ * (BFLOAT16, FLOAT16) elements bit for bit; the sum interprets them. */
+typedef enum {
+    OPTIGPU_INT32 = 0,
+    OPTIGPU_FLOAT32 = 1,
+    OPTIGPU_BFLOAT16 = 2,
+    OPTIGPU_FLOAT16 = 3
+} optigpu_dtype;
+
+typedef enum {
+    OPTIGPU_OK = 0,
+    OPTIGPU_ERR_INVALID_ARG = 1,      /* null pointer with nonzero size, negative or too large size, bad flag */
+    OPTIGPU_ERR_UNSUPPORTED_DTYPE = 2,/* dtype outside optigpu_dtype */
+    OPTIGPU_ERR_OVERLAP = 3,          /* transpose src and dst byte ranges overlap */
+    OPTIGPU_ERR_CUDA = 4,             /* a CUDA runtime call failed; see optigpu_last_error() */
+    OPTIGPU_ERR_OOM = 5,              /* a workspace or budget allocation failed */
+    OPTIGPU_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    OPTIGPU_ERR_BUSY = 7,             /* serving: no slot or memory budget left right now */
+    OPTIGPU_ERR_NOT_FOUND = 8         /* unknown ticket or handle */
+} optigpu_status;
+
+/* ------------------------------------------------------------------------ */
+/* Transpose (Listing 3.5, Sec. 3.1)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Transpose kernels.  AUTO picks the fastest eligible one for the shape. */
+typedef enum {
+    OPTIGPU_TRANSPOSE_AUTO = 0,
+    /* 32x32 shared-memory tile padded by one 4-byte bank per row, one
+     * barrier, 8 rows of threads moving 4 elements each: the classic
+     * bank-conflict-free form of the thesis's Listing 3.6 kernel (Sec. 7.1
+     * compares against this form).  Any shape, any alignment. */
+    OPTIGPU_TRANSPOSE_TILE32 = 1,
+    /* Persistent kernel: TMA 2-D tile loads into a multi-stage shared-memory
+     * ring (mbarrier completion), 16-byte micro-block transposes in
+     * registers, TMA 2-D tile stores.  Needs 16-byte aligned src/dst and
+     * rows, cols multiples of 16 / element size. */
+    OPTIGPU_TRANSPOSE_TMA = 2
+} optigpu_transpose_kernel;
+
+/* dst (cols x rows) = transpose of src (rows x cols).
+ *   src, dst  device pointers, dense row-major, esize(dtype) bytes/element;
+ *             must not overlap.  May be NULL only if rows * cols == 0.
+ *   rows, cols >= 0; rows * cols * esize < 2^62.  rows == 0 or cols == 0 is
+ *             a no-op that returns OPTIGPU_OK.
+ * Returns INVALID_ARG, UNSUPPORTED_DTYPE, OVERLAP or CUDA (launch failure). */
+optigpu_status optigpu_transpose(const void *src, void *dst, int64_t rows,
+                                 int64_t cols, optigpu_dtype dtype,
+                                 optigpu_stream_t stream);
+
+/* Same, with an explicit kernel choice.  Asking for TMA on an ineligible
+ * shape or alignment returns INVALID_ARG. */
+optigpu_status optigpu_transpose_ex(const void *src, void *dst, int64_t rows,
+                                    int64_t cols, optigpu_dtype dtype,
+                                    optigpu_transpose_kernel kernel,
+                                    optigpu_stream_t stream);
+
+/* 1 if the TMA kernel accepts this shape and these pointers, else 0. */
+int optigpu_transpose_tma_eligible(const void *src, const void *dst,
+                                   int64_t rows, int64_t cols,
+                                   optigpu_dtype dtype);
+
+/* ------------------------------------------------------------------------ */
+/* Sum reduction (Listing 2.1, Sec. 2.1; partial-sum form Listing 2.2)      */
+/* ------------------------------------------------------------------------ */
+
+/* Accumulation modes for FLOAT32 / BFLOAT16 / FLOAT16 input (INT32 input is
+ * always exact in int64).  The chunk partition and the combine order depend
+ * only on (n, dtype, flags), so repeated calls give bit-identical results. */
+#define OPTIGPU_REDUCE_PLAIN 0u       /* FP32 per-thread sums and FP32 trees */
+#define OPTIGPU_REDUCE_COMPENSATED 1u /* FP32 Neumaier per-thread sums, TwoSum trees */
+
+/* Elements per chunk: one partial sum per OPTIGPU_REDUCE_CHUNK elements
+ * (the role of the 128-element tiles of Listing 2.2). */
+#define OPTIGPU_REDUCE_CHUNK 16384
+
+/* *out = sum of src[0 .. n).
+ *   src   device pointer to n elements of dtype (any alignment; 16-byte
+ *         aligned input takes the vector path).  May be NULL if n == 0.
+ *   out   device pointer to ONE 8-byte value: int64_t for INT32 input,
+ *         double for float input.  Float partials are combined in FP64 on
+ *         the GPU (no float atomics); the FP32 value is (float)*out.
+ *   n     >= 0 and < 2^62.  n == 0 writes 0.
+ * Uses a per-stream library workspace of 8 * ceil(n / CHUNK) + 256 bytes,
+ * allocated with cudaMalloc on first use (and grown on demand), so the first
+ * call on a stream must not happen during stream capture.
+ * Returns INVALID_ARG, UNSUPPORTED_DTYPE, OOM or CUDA. */
+optigpu_status optigpu_reduce_sum(const void *src, int64_t n,
+                                  optigpu_dtype dtype, void *out,
+                                  optigpu_stream_t stream);
+
+/* Same, with accumulation flags (OPTIGPU_REDUCE_*).  Unknown flag bits
+ * return INVALID_ARG. */
+optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
+                                     optigpu_dtype dtype, void *out,
+                                     uint32_t flags, optigpu_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Status and housekeeping                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Waits for `stream`, then reports the first asynchronous CUDA error
+ * (OPTIGPU_ERR_CUDA) or a device-side wait that gave up since the last call
+ * (OPTIGPU_ERR_TIMEOUT; the device flag is per device and is cleared by this
+ * call).  OPTIGPU_OK otherwise. */
+optigpu_status optigpu_stream_status(optigpu_stream_t stream);
+
+/* Static description of a status code; never NULL. */
+const char *optigpu_status_string(optigpu_status status);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *optigpu_last_error(void);
+
+/* Device-side wait limit in nanoseconds for kernels that spin on a barrier
+ * (default 2e9, or the OPTIGPU_WAIT_LIMIT_NS environment variable). */
+void optigpu_set_wait_limit_ns(uint64_t ns);
+
+/* Frees every workspace the library holds for the current device (call with
+ * no work in flight on the library's streams). */
+optigpu_status optigpu_release_workspaces(void);
+
+/* OPTIGPU_VERSION of the loaded library. */
+int optigpu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPTIGPU_H */

@@ -1,0 +1,61 @@
+// internal.h -- host-runtime pieces shared by the library's translation units:
+// error recording, per-device facts, per-stream workspaces, the TMA
+// descriptor encoder and the device status word.  Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/optigpu.h"
+
+namespace optigpu {
+
+// Codes written to the device status word by kernels (bit flags).
+enum : unsigned {
+    DEV_ERR_WAIT_TIMEOUT = 1u,   // a bounded mbarrier / flag wait gave up
+    DEV_ERR_BAD_DESCRIPTOR = 2u, // a kernel met a work item it cannot handle
+};
+
+// Records `msg` as the calling thread's last error and returns `st`.
+optigpu_status fail(optigpu_status st, const std::string &msg);
+
+// Checks a CUDA runtime result; on failure records the message and returns
+// OPTIGPU_ERR_CUDA (OPTIGPU_ERR_OOM for allocation failures).
+optigpu_status check_cuda(cudaError_t err, const char *what);
+
+inline size_t esize_of(optigpu_dtype dt)
+{
+    return (dt == OPTIGPU_BFLOAT16 || dt == OPTIGPU_FLOAT16) ? 2 : 4;
+}
+
+inline bool dtype_valid(int dt) { return dt >= OPTIGPU_INT32 && dt <= OPTIGPU_FLOAT16; }
+
+struct DeviceInfo {
+    int device = -1;
+    int num_sms = 0;
+    size_t max_smem_optin = 0;
+    unsigned *status_word = nullptr; // device address of the status word
+};
+
+// Facts about the current device (cached per device).
+optigpu_status current_device(DeviceInfo &out);
+
+// Device-side wait limit handed to kernels that spin (ns).
+uint64_t wait_limit_ns();
+
+// A per-(device, stream) scratch buffer.  The returned pointer stays valid
+// until a later call on the same stream asks for more bytes (then it is
+// reallocated) or optigpu_release_workspaces() runs.  A new buffer is cleared
+// to zero (on `stream`), so counters kept in it start at 0.
+optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
+                                    uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
+                                    uint32_t box0, uint32_t box1);
+
+} // namespace optigpu

@@ -1,0 +1,169 @@
+// reduce.cu -- tree-based sum reduction, *out = sum of src[0 .. n)
+// (thesis arxiv 2605.13864, Listing 2.1, Sec. 2.1: reduce_sum(N, A); the
+// partial-sum form of Listing 2.2, Sec. 2.2.1; the tree of Sec. 7.2).
+//
+// One kernel does both passes:
+//
+//  pass 1  The input is cut into chunks of CHUNK = 16384 elements (the role of
+//          Listing 2.2's 128-element tiles).  CTAs of 256 threads take chunks
+//          c = blockIdx.x, blockIdx.x + gridDim.x, ...; inside a chunk thread t
+//          owns the 16-byte vectors t, t + 256, t + 512, ... and keeps a
+//          register accumulator across them (the `mySum` register accumulator
+//          whose absence costs the thesis's generated kernel ~50 GB/s,
+//          Sec. 7.2).  The elements of one vector are added in a fixed
+//          pairwise tree.  Threads are then combined by warp shuffles
+//          (butterfly, 5 steps) and the 8 warp sums by a second shuffle tree,
+//          giving one partial per chunk in partials[c]:
+//            int32 input   int64 everywhere (exact);
+//            float input   FP32 sums, widened to FP64 for the partial;
+//            compensated   FP32 Neumaier (s, c) pairs per thread, pairs
+//                          combined with Knuth's TwoSum, partial = s + c in
+//                          FP64.
+//  pass 2  The last CTA to finish (an integer completion counter; no float
+//          atomics) sums partials[0 .. num_chunks) in FP64 / int64 in a
+//          fixed order -- per-thread strided sequential sums, then the same
+//          shuffle trees -- writes *out and resets the counter.
+//
+// The chunk partition, the per-chunk order and the final order depend only
+// on (n, dtype, flags): not on the grid size, so results are bit-identical
+// from run to run and between this entry point and the batched kernel.
+#include <algorithm>
+#include <mutex>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "reduce_core.cuh"
+
+namespace optigpu {
+namespace {
+
+template <int DT, bool COMP>
+__global__ void __launch_bounds__(kReduceThreads)
+reduce_sum_kernel(const void *__restrict__ src, int64_t n, int vec_ok, void *partials,
+                  unsigned *counter, void *out, int64_t num_chunks)
+{
+    using Core = ReduceCore<DT, COMP>;
+    __shared__ typename Core::Shared sh;
+    __shared__ int s_last;
+    for (int64_t c = blockIdx.x; c < num_chunks; c += gridDim.x) {
+        const auto part = Core::chunk_partial(src, n, c, vec_ok != 0, sh);
+        if (threadIdx.x == 0)
+            Core::store_partial(partials, c, part);
+    }
+    // Completion: publish this CTA's partials, count it, and let the last CTA
+    // run the final combine.
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    Core::final_combine(partials, num_chunks, out, sh);
+    if (threadIdx.x == 0)
+        *counter = 0u;
+}
+
+struct KernelFacts {
+    bool ready = false;
+    int ctas_per_sm = 0;
+};
+std::mutex g_mu;
+KernelFacts g_facts[64][4][2];
+
+template <int DT, bool COMP>
+optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream)
+{
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const void *fn = reinterpret_cast<const void *>(&reduce_sum_kernel<DT, COMP>);
+    int ctas_per_sm = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        KernelFacts &f = g_facts[dev.device & 63][DT][COMP ? 1 : 0];
+        if (!f.ready) {
+            int k = 0;
+            st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, kReduceThreads, 0),
+                            "cudaOccupancyMaxActiveBlocksPerMultiprocessor(reduce)");
+            if (st != OPTIGPU_OK)
+                return st;
+            f.ctas_per_sm = std::max(k, 1);
+            f.ready = true;
+        }
+        ctas_per_sm = f.ctas_per_sm;
+    }
+    const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
+    void *ws = nullptr;
+    const size_t bytes = kReduceCounterBytes + size_t(num_chunks) * 8;
+    if ((st = stream_workspace(stream, bytes, &ws)) != OPTIGPU_OK)
+        return st;
+    unsigned *counter = static_cast<unsigned *>(ws);
+    void *partials = static_cast<char *>(ws) + kReduceCounterBytes;
+    const int64_t grid = std::min<int64_t>(num_chunks, int64_t(ctas_per_sm) * dev.num_sms);
+    const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
+    reduce_sum_kernel<DT, COMP><<<unsigned(grid), kReduceThreads, 0, stream>>>(src, n, vec_ok, partials,
+                                                                             counter, out, num_chunks);
+    return check_cuda(cudaGetLastError(), "launch reduce");
+}
+
+} // namespace
+
+optigpu_status reduce_dispatch(const void *src, int64_t n, int dtype, void *out, uint32_t flags,
+                               cudaStream_t stream)
+{
+    if (!dtype_valid(dtype))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce: unknown dtype " + std::to_string(dtype));
+    if (flags & ~OPTIGPU_REDUCE_COMPENSATED)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: unknown flag bits");
+    if (n < 0 || n > (int64_t(1) << 62))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: n out of range");
+    if (!out)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: null out");
+    if (n > 0 && !src)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: null src");
+    if (n > 0 && reinterpret_cast<uintptr_t>(src) % esize_of(optigpu_dtype(dtype)))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: src not aligned to the element size");
+    if (reinterpret_cast<uintptr_t>(out) % 8)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce: out not 8-byte aligned");
+    if (n == 0)
+        return check_cuda(cudaMemsetAsync(out, 0, 8, stream), "reduce: write 0");
+    const bool comp = (flags & OPTIGPU_REDUCE_COMPENSATED) != 0;
+    switch (dtype) {
+    case OPTIGPU_INT32: return launch<OPTIGPU_INT32, false>(src, n, out, stream);
+    case OPTIGPU_FLOAT32:
+        return comp ? launch<OPTIGPU_FLOAT32, true>(src, n, out, stream)
+                    : launch<OPTIGPU_FLOAT32, false>(src, n, out, stream);
+    case OPTIGPU_BFLOAT16:
+        return comp ? launch<OPTIGPU_BFLOAT16, true>(src, n, out, stream)
+                    : launch<OPTIGPU_BFLOAT16, false>(src, n, out, stream);
+    default:
+        return comp ? launch<OPTIGPU_FLOAT16, true>(src, n, out, stream)
+                    : launch<OPTIGPU_FLOAT16, false>(src, n, out, stream);
+    }
+}
+
+} // namespace optigpu
+
+using namespace optigpu;
+
+extern "C" {
+
+optigpu_status optigpu_reduce_sum(const void *src, int64_t n, optigpu_dtype dtype, void *out,
+                                  optigpu_stream_t stream)
+{
+    return reduce_dispatch(src, n, int(dtype), out, OPTIGPU_REDUCE_PLAIN, static_cast<cudaStream_t>(stream));
+}
+
+optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n, optigpu_dtype dtype, void *out,
+                                     uint32_t flags, optigpu_stream_t stream)
+{
+    return reduce_dispatch(src, n, int(dtype), out, flags, static_cast<cudaStream_t>(stream));
+}
+
+} // extern "C"

@@ -13,11 +13,11 @@ one GB300):
 * ``small``      -- 1024x1024 int32 in [-1000, 1000], seed 0; the same matrix
   is transposed and summed.
 * ``roofline``   -- 16384x16384 float32 N(0,1) transpose and a 2^28 float32
-  N(0,1) vector, seed 1 (the vector is the next 2^28 draws of the same
-  generator).
+  N(0,1) vector, seed 1 (the vector from an independent sub-stream of the
+  seed, so either can be drawn alone).
 * ``precision``  -- 2^28 draws of N(100,1), seed 2, rounded to bfloat16 and,
-  separately, to float16; then an 8192x8192 bfloat16 N(0,1) matrix from the
-  same generator.
+  separately, to float16; an 8192x8192 bfloat16 N(0,1) matrix from an
+  independent sub-stream of seed 2.
 * ``batched``    -- 4096 instances, seed 3: transposes of float32 matrices
   with rows and cols log-uniform in [1, 2048] and float32 sums with lengths
   log-uniform in [1, 2^22], interleaved T, R, T, R, ...
@@ -98,28 +98,32 @@ def small(rows: int = 1024, cols: int = 1024) -> np.ndarray:
     return rng.integers(-1000, 1001, size=(rows, cols), dtype=np.int32)
 
 
-def roofline(rows: int = 16384, cols: int = 16384, n: int = 1 << 28):
-    """(matrix, vector): float32 N(0,1), seed 1; the vector follows the matrix."""
-    rng = np.random.default_rng(1)
-    mat = rng.standard_normal(size=(rows, cols), dtype=np.float32)
-    vec = rng.standard_normal(size=(n,), dtype=np.float32)
-    return mat, vec
+def _substream(seed: int, k: int) -> np.random.Generator:
+    """Independent generator number k of workload `seed` (PCG64 spawn key)."""
+    return np.random.default_rng(np.random.SeedSequence(entropy=seed, spawn_key=(k,)))
 
 
-def precision(n: int = 1 << 28, side: int = 8192):
-    """(bf16 vector, fp16 vector, bf16 matrix) as uint16 bit patterns, seed 2.
+def roofline_matrix(rows: int = 16384, cols: int = 16384) -> np.ndarray:
+    """float32 N(0,1), seed 1."""
+    return np.random.default_rng(1).standard_normal(size=(rows, cols), dtype=np.float32)
 
-    The vectors are the same 2^28 draws of N(100, 1) rounded two ways; the
-    matrix is N(0, 1) drawn next.
-    """
-    rng = np.random.default_rng(2)
-    x = rng.standard_normal(size=(n,), dtype=np.float32) + np.float32(100.0)
-    vb = _round_to_16(x, "bfloat16")
-    vh = _round_to_16(x, "float16")
-    del x
-    m = rng.standard_normal(size=(side, side), dtype=np.float32)
-    mb = _round_to_16(m, "bfloat16").reshape(side, side)
-    return vb, vh, mb
+
+def roofline_vector(n: int = 1 << 28) -> np.ndarray:
+    """float32 N(0,1), seed 1, sub-stream 1 (independent of the matrix)."""
+    return _substream(1, 1).standard_normal(size=(n,), dtype=np.float32)
+
+
+def precision_vectors(n: int = 1 << 28):
+    """(bf16, fp16) bit patterns of the same n draws of N(100, 1), seed 2."""
+    x = np.random.default_rng(2).standard_normal(size=(n,), dtype=np.float32)
+    x += np.float32(100.0)
+    return _round_to_16(x, "bfloat16"), _round_to_16(x, "float16")
+
+
+def precision_matrix(side: int = 8192) -> np.ndarray:
+    """bfloat16 N(0, 1) bit patterns, seed 2, sub-stream 1."""
+    m = _substream(2, 1).standard_normal(size=(side, side), dtype=np.float32)
+    return _round_to_16(m, "bfloat16").reshape(side, side)
 
 
 def log_uniform(rng: np.random.Generator, hi: int, size: int) -> np.ndarray:

@@ -1,0 +1,117 @@
+"""The C-ABI library builds, loads and exports every symbol include/optigpu.h
+declares; host-side argument validation answers without touching a GPU.
+
+No compute call is made here: every call below is rejected (or answered) by
+the host before any CUDA API is reached.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_13864_gb300 import _native as N
+from paper_2605_13864_gb300 import build_lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "optigpu.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(optigpu_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return N.load(build=True)
+
+
+def test_header_declares_the_core_calls():
+    names = declared_functions()
+    for must in ("optigpu_transpose", "optigpu_reduce_sum", "optigpu_reduce_sum_ex",
+                 "optigpu_stream_status", "optigpu_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(build_lib.LIB)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(N.SIGNATURES)
+
+
+def test_library_is_built_for_sm_103a_only():
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_and_status_strings(lib):
+    assert lib.optigpu_version() == 100
+    for code in range(0, 9):
+        assert lib.optigpu_status_string(code)
+    assert lib.optigpu_status_string(0) == b"ok"
+
+
+FAKE = 0x7F0000000000  # never dereferenced: validation rejects first
+
+
+@pytest.mark.parametrize("args,status", [
+    ((None, None, -1, 4, N.FLOAT32), N.ERR_INVALID_ARG),
+    ((None, None, 4, -1, N.FLOAT32), N.ERR_INVALID_ARG),
+    ((None, None, 4, 4, N.FLOAT32), N.ERR_INVALID_ARG),
+    ((FAKE, FAKE + (1 << 20), 4, 4, 9), N.ERR_UNSUPPORTED_DTYPE),
+    ((FAKE, FAKE + 8, 4, 4, N.FLOAT32), N.ERR_OVERLAP),
+    ((FAKE + 8, FAKE, 4, 4, N.BFLOAT16), N.ERR_OVERLAP),
+    ((FAKE, FAKE + 64, 1 << 40, 1 << 40, N.FLOAT32), N.ERR_INVALID_ARG),
+    ((FAKE + 2, FAKE + (1 << 20), 4, 4, N.FLOAT32), N.ERR_INVALID_ARG),  # not element-aligned
+    ((FAKE, FAKE + (1 << 20) + 1, 4, 4, N.FLOAT16), N.ERR_INVALID_ARG),
+    ((None, None, 0, 5, N.FLOAT32), N.OK),   # empty: a no-op
+    ((None, None, 7, 0, N.INT32), N.OK),
+])
+def test_transpose_validation(lib, args, status):
+    src, dst, rows, cols, dt = args
+    assert lib.optigpu_transpose(src, dst, rows, cols, dt, None) == status
+
+
+def test_transpose_ex_rejects_unknown_kernel(lib):
+    assert lib.optigpu_transpose_ex(FAKE, FAKE + (1 << 20), 4, 4, N.FLOAT32, 7, None) == N.ERR_INVALID_ARG
+
+
+def test_transpose_ex_rejects_tma_on_ineligible_shape(lib):
+    # cols = 3 floats is not a multiple of 16 bytes
+    assert lib.optigpu_transpose_ex(FAKE, FAKE + (1 << 20), 4, 3, N.FLOAT32, N.TRANSPOSE_TMA,
+                                    None) == N.ERR_INVALID_ARG
+    assert b"TMA" in lib.optigpu_last_error()
+
+
+@pytest.mark.parametrize("rows,cols,dt,align,ok", [
+    (64, 64, N.FLOAT32, 0, 1), (4, 8, N.INT32, 0, 1), (8, 16, N.BFLOAT16, 0, 1),
+    (4, 4, N.BFLOAT16, 0, 0), (3, 64, N.FLOAT32, 0, 0), (64, 64, N.FLOAT32, 4, 0),
+    (0, 64, N.FLOAT32, 0, 0),
+])
+def test_tma_eligibility(lib, rows, cols, dt, align, ok):
+    assert lib.optigpu_transpose_tma_eligible(FAKE + align, FAKE + (1 << 30), rows, cols, dt) == ok
+
+
+@pytest.mark.parametrize("args,status", [
+    ((FAKE, -1, N.FLOAT32, FAKE, 0), N.ERR_INVALID_ARG),
+    ((FAKE, 10, 17, FAKE, 0), N.ERR_UNSUPPORTED_DTYPE),
+    ((FAKE, 10, N.FLOAT32, None, 0), N.ERR_INVALID_ARG),
+    ((None, 10, N.FLOAT32, FAKE, 0), N.ERR_INVALID_ARG),
+    ((FAKE, 10, N.FLOAT32, FAKE, 6), N.ERR_INVALID_ARG),
+    ((FAKE, (1 << 62) + 1, N.INT32, FAKE, 0), N.ERR_INVALID_ARG),
+    ((FAKE + 2, 10, N.FLOAT32, FAKE, 0), N.ERR_INVALID_ARG),   # src not element-aligned
+    ((FAKE + 1, 10, N.BFLOAT16, FAKE, 0), N.ERR_INVALID_ARG),
+    ((FAKE, 10, N.FLOAT32, FAKE + 4, 0), N.ERR_INVALID_ARG),   # out not 8-byte aligned
+])
+def test_reduce_validation(lib, args, status):
+    src, n, dt, out, flags = args
+    assert lib.optigpu_reduce_sum_ex(src, n, dt, out, flags, None) == status
+
+
+def test_errors_carry_a_message(lib):
+    lib.optigpu_reduce_sum_ex(FAKE, 10, 17, FAKE, 0, None)
+    assert b"dtype" in lib.optigpu_last_error()
