@@ -145,6 +145,58 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
                                      uint32_t flags, optigpu_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Autotuning                                                               */
+/* ------------------------------------------------------------------------ */
+/* The thesis fixes its launch parameters by hand (the tile size 32 and the
+ * 128-element chunk in its transformation scripts, Sec. 2.2.1 and 3.2); this
+ * library compiles several configurations of each kernel (tile shape,
+ * pipeline depth, output buffers; CTAs per SM for the sum) and picks among
+ * them by measurement.  Selections are process-wide.  None of them changes a
+ * result: transposes are bit copies and the sum's chunk partition is fixed. */
+
+typedef enum {
+    OPTIGPU_OP_TRANSPOSE = 0,
+    OPTIGPU_OP_REDUCE = 1
+} optigpu_op;
+
+/* Number of configurations of `op` for `dtype` (-1 for a bad op or dtype).
+ * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel. */
+int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype);
+
+/* Static name of configuration `config`, or NULL if out of range. */
+const char *optigpu_tune_config_name(optigpu_op op, optigpu_dtype dtype, int config);
+
+/* Selects the configuration AUTO uses from now on.  For the transpose the
+ * choice is per element size (INT32 and FLOAT32 share one, BFLOAT16 and
+ * FLOAT16 the other).  INVALID_ARG for an index out of range. */
+optigpu_status optigpu_tune_select(optigpu_op op, optigpu_dtype dtype, int config);
+
+/* Currently selected configuration index (-1 for a bad op or dtype). */
+int optigpu_tune_selected(optigpu_op op, optigpu_dtype dtype);
+
+/* Named integer parameters: "transpose.group_rows" (tile-rows the TMA
+ * transpose walks before moving one tile-column right, 1..4096, default 16).
+ * NOT_FOUND for an unknown name. */
+optigpu_status optigpu_tune_set_param(const char *name, int64_t value);
+int64_t optigpu_tune_get_param(const char *name); /* -1 if unknown */
+
+/* Times every configuration of `op` on a rows x cols problem (the sum uses
+ * n = rows * cols) in library-owned scratch memory (cudaMalloc'd and freed
+ * inside the call), `reps` timed launches each after two warm-ups, median of
+ * CUDA-event times on `stream`; selects the fastest and returns its index
+ * and time.  Transpose TMA configurations are skipped when the shape is not
+ * TMA-eligible.  Synchronises `stream`.  Must not run during stream capture. */
+optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows, int64_t cols,
+                                int reps, optigpu_stream_t stream, int *best_config,
+                                float *best_ms);
+
+/* Writes / reads the current selections as a small text file.  A cache
+ * named by the OPTIGPU_TUNE_CACHE environment variable is read when the
+ * library is loaded. */
+optigpu_status optigpu_tune_save(const char *path);
+optigpu_status optigpu_tune_load(const char *path);
+
+/* ------------------------------------------------------------------------ */
 /* Status and housekeeping                                                  */
 /* ------------------------------------------------------------------------ */
 

@@ -33,6 +33,8 @@ INT32, FLOAT32, BFLOAT16, FLOAT16 = 0, 1, 2, 3
 # optigpu_transpose_kernel
 TRANSPOSE_AUTO, TRANSPOSE_TILE32, TRANSPOSE_TMA = 0, 1, 2
 
+OP_TRANSPOSE, OP_REDUCE = 0, 1
+
 REDUCE_PLAIN = 0
 REDUCE_COMPENSATED = 1
 REDUCE_CHUNK = 16384
@@ -45,6 +47,16 @@ SIGNATURES = {
     "optigpu_transpose_tma_eligible": (_ci, [_vp, _vp, _i64, _i64, _ci]),
     "optigpu_reduce_sum": (_ci, [_vp, _i64, _ci, _vp, _vp]),
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
+    "optigpu_tune_num_configs": (_ci, [_ci, _ci]),
+    "optigpu_tune_config_name": (ctypes.c_char_p, [_ci, _ci, _ci]),
+    "optigpu_tune_select": (_ci, [_ci, _ci, _ci]),
+    "optigpu_tune_selected": (_ci, [_ci, _ci]),
+    "optigpu_tune_set_param": (_ci, [ctypes.c_char_p, _i64]),
+    "optigpu_tune_get_param": (_i64, [ctypes.c_char_p]),
+    "optigpu_autotune": (_ci, [_ci, _ci, _i64, _i64, _ci, _vp, ctypes.POINTER(_ci),
+                              ctypes.POINTER(ctypes.c_float)]),
+    "optigpu_tune_save": (_ci, [ctypes.c_char_p]),
+    "optigpu_tune_load": (_ci, [ctypes.c_char_p]),
     "optigpu_stream_status": (_ci, [_vp]),
     "optigpu_status_string": (ctypes.c_char_p, [_ci]),
     "optigpu_last_error": (ctypes.c_char_p, []),

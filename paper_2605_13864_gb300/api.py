@@ -99,3 +99,47 @@ def set_wait_limit_ns(ns: int) -> None:
 
 def release_workspaces() -> None:
     N.check(N.lib().optigpu_release_workspaces(), "optigpu_release_workspaces")
+
+
+# ---------------------------------------------------------------- autotuning
+
+_OPS = {"transpose": N.OP_TRANSPOSE, "reduce": N.OP_REDUCE}
+
+
+def tune_configs(op: str, dtype: torch.dtype) -> list[str]:
+    """Names of the compiled configurations of ``op`` for ``dtype``."""
+    L = N.lib()
+    n = L.optigpu_tune_num_configs(_OPS[op], dtype_code(dtype))
+    return [L.optigpu_tune_config_name(_OPS[op], dtype_code(dtype), i).decode() for i in range(n)]
+
+
+def tune_select(op: str, dtype: torch.dtype, config: int) -> None:
+    N.check(N.lib().optigpu_tune_select(_OPS[op], dtype_code(dtype), int(config)), "optigpu_tune_select")
+
+
+def tune_selected(op: str, dtype: torch.dtype) -> int:
+    return int(N.lib().optigpu_tune_selected(_OPS[op], dtype_code(dtype)))
+
+
+def tune_set_param(name: str, value: int) -> None:
+    N.check(N.lib().optigpu_tune_set_param(name.encode(), int(value)), "optigpu_tune_set_param")
+
+
+def autotune(op: str, dtype: torch.dtype, rows: int, cols: int = 1, reps: int = 10, stream=None):
+    """Times every configuration on a rows x cols problem; selects and returns
+    ``(index, name, ms)`` of the fastest."""
+    import ctypes
+    best = ctypes.c_int(-1)
+    ms = ctypes.c_float(0.0)
+    N.check(N.lib().optigpu_autotune(_OPS[op], dtype_code(dtype), int(rows), int(cols), int(reps),
+                                     _stream_ptr(stream), ctypes.byref(best), ctypes.byref(ms)),
+            "optigpu_autotune")
+    return best.value, tune_configs(op, dtype)[best.value], float(ms.value)
+
+
+def tune_save(path: str) -> None:
+    N.check(N.lib().optigpu_tune_save(path.encode()), "optigpu_tune_save")
+
+
+def tune_load(path: str) -> None:
+    N.check(N.lib().optigpu_tune_load(path.encode()), "optigpu_tune_load")

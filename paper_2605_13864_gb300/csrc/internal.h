@@ -58,4 +58,23 @@ optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDat
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
                                     uint32_t box0, uint32_t box1);
 
+// Transpose configurations: indices 0 .. n-2 are TMA kernels, n-1 is tile32.
+int transpose_num_configs(size_t esize);
+const char *transpose_config_name(size_t esize, int config);
+int transpose_selected(size_t esize);
+void transpose_select(size_t esize, int config);
+void transpose_set_group_rows(int g);
+int transpose_group_rows();
+optigpu_status transpose_launch_config(const void *src, void *dst, int64_t rows, int64_t cols, size_t esize,
+                                       int config, cudaStream_t stream);
+
+// Reduction configurations: CTAs per SM of the persistent grid (0 = as many
+// as fit).  The result does not depend on the choice.
+int reduce_num_configs();
+const char *reduce_config_name(int config);
+int reduce_selected();
+void reduce_select(int config);
+optigpu_status reduce_dispatch(const void *src, int64_t n, int dtype, void *out, uint32_t flags,
+                               cudaStream_t stream);
+
 } // namespace optigpu

@@ -28,6 +28,7 @@
 // on (n, dtype, flags): not on the grid size, so results are bit-identical
 // from run to run and between this entry point and the batched kernel.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include <cuda_bf16.h>
@@ -68,6 +69,13 @@ reduce_sum_kernel(const void *__restrict__ src, int64_t n, int vec_ok, void *par
         *counter = 0u;
 }
 
+// CTAs per SM of the persistent grid for each configuration (0 = as many as
+// fit); the partition into chunks, and so the result, does not depend on it.
+constexpr int kReduceCtasPerSm[] = {0, 2, 3, 4, 6};
+constexpr const char *kReduceConfigNames[] = {"reduce ctas/SM=max", "reduce ctas/SM=2", "reduce ctas/SM=3",
+                                              "reduce ctas/SM=4", "reduce ctas/SM=6"};
+std::atomic<int> g_reduce_choice{0};
+
 struct KernelFacts {
     bool ready = false;
     int ctas_per_sm = 0;
@@ -98,6 +106,9 @@ optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream
         }
         ctas_per_sm = f.ctas_per_sm;
     }
+    const int cap = kReduceCtasPerSm[g_reduce_choice.load()];
+    if (cap > 0)
+        ctas_per_sm = std::min(ctas_per_sm, cap);
     const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
     void *ws = nullptr;
     const size_t bytes = kReduceCounterBytes + size_t(num_chunks) * 8;
@@ -113,6 +124,17 @@ optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream
 }
 
 } // namespace
+
+int reduce_num_configs() { return int(sizeof(kReduceCtasPerSm) / sizeof(kReduceCtasPerSm[0])); }
+
+const char *reduce_config_name(int config)
+{
+    return (config >= 0 && config < reduce_num_configs()) ? kReduceConfigNames[config] : nullptr;
+}
+
+int reduce_selected() { return g_reduce_choice.load(); }
+
+void reduce_select(int config) { g_reduce_choice.store(config); }
 
 optigpu_status reduce_dispatch(const void *src, int64_t n, int dtype, void *out, uint32_t flags,
                                cudaStream_t stream)

@@ -28,7 +28,12 @@
 //    both the read and the write side, which makes the tile conflict-free
 //    without a swizzle.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -115,104 +120,146 @@ struct TmaTile {
     static constexpr int V = 16 / ESIZE;        // elements per 16-byte vector
     static constexpr int MR = TR / V;           // micro-block rows
     static constexpr int MC = TC / V;           // micro-block columns
-    static constexpr int THREADS = MR * MC;     // one micro-block per thread
+    static constexpr int THREADS = MR * MC;     // one micro-block per consumer thread
     static constexpr uint32_t BYTES = TR * TC * ESIZE;
     static constexpr uint32_t IN_PITCH = TC * ESIZE;  // source tile row
     static constexpr uint32_t OUT_PITCH = TR * ESIZE; // output tile row
     static_assert(MR % 8 == 0 && MC % 8 == 0, "micro-block grid must be a multiple of 8");
     static_assert(IN_PITCH % 128 == 0 && OUT_PITCH % 128 == 0, "tile rows must span whole bank cycles");
     static_assert(TR <= 256 && TC <= 256, "TMA box dimensions are at most 256");
+    static_assert(THREADS % 32 == 0 && THREADS <= 512, "consumer threads");
 };
 
-template <int ESIZE, int TR, int TC, int STAGES>
-__global__ void __launch_bounds__(TmaTile<ESIZE, TR, TC>::THREADS)
+// Tile order.  Tile ids run down `group` tile-rows before moving one
+// tile-column right, so the CTAs working at one moment (consecutive ids)
+// cover a block of group x (CTAs / group) tiles: each source row band is read
+// in runs of several KB and each destination row is written in runs of
+// group x TR elements, instead of one short piece per destination row.
+struct TileOrder {
+    int32_t tiles_r, tiles_c, group;
+    __device__ __forceinline__ void coords(int64_t id, int32_t &tr, int32_t &tc) const
+    {
+        const int64_t per_group = int64_t(group) * tiles_c;
+        const int32_t g = int32_t(id / per_group);
+        const int32_t within = int32_t(id - int64_t(g) * per_group);
+        const int32_t rows_here = min(group, tiles_r - g * group);
+        tc = within / rows_here;
+        tr = g * group + (within - tc * rows_here);
+    }
+};
+
+// Warp roles: warps 0 .. THREADS/32 - 1 are consumers (one micro-block per
+// thread); the last warp is the producer, whose lane 0 keeps the STAGES-deep
+// ring of source tiles full.  Per stage s: full[s] completes when the TMA
+// load has landed (transaction bytes), empty[s] when every consumer warp has
+// taken its micro-blocks out.  NOB output buffers let up to NOB - 1 tile
+// stores still read shared memory while the next tile is written.
+template <int ESIZE, int TR, int TC, int STAGES, int NOB>
+__global__ void __launch_bounds__(TmaTile<ESIZE, TR, TC>::THREADS + 32, 1)
 transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
-                     const __grid_constant__ CUtensorMap tm_dst, int32_t tiles_c,
+                     const __grid_constant__ CUtensorMap tm_dst, TileOrder order,
                      int64_t num_tiles, uint64_t wait_limit_ns, unsigned *status)
 {
     using Tile = TmaTile<ESIZE, TR, TC>;
     constexpr int V = Tile::V;
+    constexpr uint32_t NCONS = Tile::THREADS;
+    constexpr uint32_t NWARPS_CONS = NCONS / 32;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t in_base = ptx::smem_addr(smem);
     const uint32_t out_base = in_base + STAGES * Tile::BYTES;
-    const uint32_t bar_base = out_base + 2 * Tile::BYTES;
+    const uint32_t full_bar = out_base + NOB * Tile::BYTES;
+    const uint32_t empty_bar = full_bar + 8u * STAGES;
 
-    // Micro-block of this thread.  With q = t % 8 and p = t / 8, the 8
-    // threads of a wavefront share p and get rb % 8 = q and
-    // cb % 8 = (q + p) % 8: distinct 16-byte bank groups on both sides.
     const int t = threadIdx.x;
-    const int q = t & 7, p = t >> 3;
-    const int rest = p >> 3;
-    const int rb = (rest % (Tile::MR / 8)) * 8 + q;
-    const int cb = (rest / (Tile::MR / 8)) * 8 + ((q + (p & 7)) & 7);
-    const uint32_t rd_off = uint32_t(rb * V) * Tile::IN_PITCH + uint32_t(cb) * 16u;
-    const uint32_t wr_off = uint32_t(cb * V) * Tile::OUT_PITCH + uint32_t(rb) * 16u;
-
     const int64_t first = blockIdx.x, stride = gridDim.x;
     const int64_t my_count = first < num_tiles ? (num_tiles - 1 - first) / stride + 1 : 0;
 
     if (t == 0) {
         ptx::prefetch_tensormap(&tm_src);
         ptx::prefetch_tensormap(&tm_dst);
-        for (int s = 0; s < STAGES; ++s)
-            ptx::mbar_init(bar_base + 8u * s, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(full_bar + 8u * s, 1);
+            ptx::mbar_init(empty_bar + 8u * s, NWARPS_CONS);
+        }
         ptx::fence_mbar_init();
     }
     __syncthreads();
 
-    auto issue_load = [&](int64_t k) {
-        const int64_t tile = first + k * stride;
-        const int32_t tr = int32_t(tile / tiles_c);
-        const int32_t tc = int32_t(tile - int64_t(tr) * tiles_c);
-        const uint32_t s = uint32_t(k % STAGES);
-        ptx::mbar_arrive_expect_tx(bar_base + 8u * s, Tile::BYTES);
-        ptx::tma_load_2d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, bar_base + 8u * s);
-    };
+    if (uint32_t(t) >= NCONS) {
+        // ------------------------------------------------------ producer
+        if (t != int(NCONS))
+            return;
+        int64_t k = 0;
+        for (; k < my_count; ++k) {
+            const uint32_t s = uint32_t(k % STAGES);
+            if (k >= STAGES &&
+                !ptx::mbar_wait_bounded(empty_bar + 8u * s, uint32_t(k / STAGES - 1) & 1u, wait_limit_ns)) {
+                atomicOr(status, DEV_ERR_WAIT_TIMEOUT);
+                break;
+            }
+            int32_t tr, tc;
+            order.coords(first + k * stride, tr, tc);
+            ptx::mbar_arrive_expect_tx(full_bar + 8u * s, Tile::BYTES);
+            ptx::tma_load_2d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, full_bar + 8u * s);
+        }
+        // Before leaving, let every load still in flight land (bounded), so no
+        // copy targets this CTA's shared memory after the consumers are gone.
+        for (int64_t kk = (k > STAGES ? k - STAGES : 0); kk < k; ++kk)
+            ptx::mbar_wait_bounded(full_bar + 8u * uint32_t(kk % STAGES), uint32_t(kk / STAGES) & 1u,
+                                   wait_limit_ns);
+        return;
+    }
 
-    if (t == 0)
-        for (int64_t k = 0; k < STAGES && k < my_count; ++k)
-            issue_load(k);
+    // ---------------------------------------------------------- consumers
+    // Micro-block of this thread.  With q = t % 8 and p = t / 8, the 8
+    // threads of a shared-memory wavefront (one quarter warp, 16-byte
+    // accesses) share p and get rb % 8 = q and cb % 8 = (q + p) % 8: distinct
+    // 16-byte bank groups on both the read and the write side.
+    const int q = t & 7, p = t >> 3;
+    const int rest = p >> 3;
+    const int rb = (rest % (Tile::MR / 8)) * 8 + q;
+    const int cb = (rest / (Tile::MR / 8)) * 8 + ((q + (p & 7)) & 7);
+    const uint32_t rd_off = uint32_t(rb * V) * Tile::IN_PITCH + uint32_t(cb) * 16u;
+    const uint32_t wr_off = uint32_t(cb * V) * Tile::OUT_PITCH + uint32_t(rb) * 16u;
+    const bool lane0 = (t & 31) == 0;
 
     for (int64_t k = 0; k < my_count; ++k) {
         const uint32_t s = uint32_t(k % STAGES);
-        const uint32_t parity = uint32_t(k / STAGES) & 1u;
-        const bool ok = ptx::mbar_wait_bounded(bar_base + 8u * s, parity, wait_limit_ns);
+        const bool ok = ptx::mbar_wait_bounded(full_bar + 8u * s, uint32_t(k / STAGES) & 1u, wait_limit_ns);
         uint4 r[V];
         if (ok) {
 #pragma unroll
             for (int i = 0; i < V; ++i)
                 r[i] = ptx::lds_v4(in_base + s * Tile::BYTES + rd_off + uint32_t(i) * Tile::IN_PITCH);
         }
-        // All threads agree on whether to stop.  This barrier also (a) frees
-        // stage s for the next load and (b) publishes thread 0's wait for the
-        // store that last used the output buffer written below.
-        if (__syncthreads_or(!ok)) {
+        // Output buffer k % NOB is free once the store issued NOB tiles ago
+        // has read it: thread 0 (the only thread that issues stores) waits,
+        // and the barrier below publishes that to every consumer.  The same
+        // barrier lets all consumers agree on a timeout.
+        if (t == 0)
+            ptx::bulk_wait_group_read<NOB - 1>();
+        if (ptx::named_bar_or(1, NCONS, !ok)) {
             if (t == 0) {
                 atomicOr(status, DEV_ERR_WAIT_TIMEOUT);
-                // Let the loads already issued land (bounded) before exiting.
-                for (int64_t kk = k; kk < k + STAGES && kk < my_count; ++kk)
-                    ptx::mbar_wait_bounded(bar_base + 8u * uint32_t(kk % STAGES),
-                                           uint32_t(kk / STAGES) & 1u, wait_limit_ns);
                 ptx::bulk_wait_group<0>();
             }
             return;
         }
-        if (t == 0 && k + STAGES < my_count)
-            issue_load(k + STAGES);
-
-        const uint32_t obuf = out_base + uint32_t(k & 1) * Tile::BYTES;
+        const uint32_t obuf = out_base + uint32_t(k % NOB) * Tile::BYTES;
         store_transposed<ESIZE>(r, obuf + wr_off, Tile::OUT_PITCH);
+        // The values just stored came from stage s, so every lane's read of
+        // it is complete: release the stage to the producer, one arrival per
+        // warp.
+        __syncwarp();
+        if (lane0)
+            ptx::mbar_arrive(empty_bar + 8u * s);
         ptx::fence_proxy_async_smem();
-        __syncthreads();
+        ptx::named_bar_sync(2, NCONS);
         if (t == 0) {
-            const int64_t tile = first + k * stride;
-            const int32_t tr = int32_t(tile / tiles_c);
-            const int32_t tc = int32_t(tile - int64_t(tr) * tiles_c);
+            int32_t tr, tc;
+            order.coords(first + k * stride, tr, tc);
             ptx::tma_store_2d(&tm_dst, tr * TR, tc * TC, obuf);
             ptx::bulk_commit_group();
-            // The buffer used next iteration was read by the store before
-            // this one; wait until at most this store is still reading.
-            ptx::bulk_wait_group_read<1>();
         }
     }
     if (t == 0)
@@ -223,30 +270,48 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
 
 struct TmaConfig {
     int esize;
-    int tr, tc, stages, threads;
+    int tr, tc, stages, nob, threads;
     uint32_t tile_bytes;
     const void *fn;
+    const char *name;
 };
 
-template <int ESIZE, int TR, int TC, int STAGES>
-TmaConfig make_config()
+template <int ESIZE, int TR, int TC, int STAGES, int NOB>
+TmaConfig make_config(const char *name)
 {
     using Tile = TmaTile<ESIZE, TR, TC>;
-    return TmaConfig{ESIZE, TR, TC, STAGES, Tile::THREADS, Tile::BYTES,
-                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES>)};
+    return TmaConfig{ESIZE, TR, TC, STAGES, NOB, Tile::THREADS + 32, Tile::BYTES,
+                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB>), name};
 }
 
-const TmaConfig &tma_config(size_t esize)
+// The compiled TMA configurations per element size; index 0 is the default.
+const std::vector<TmaConfig> &tma_configs(size_t esize)
 {
-    static const TmaConfig c4 = make_config<4, 64, 64, 4>();
-    static const TmaConfig c2 = make_config<2, 64, 128, 4>();
+    static const std::vector<TmaConfig> c4 = {
+        make_config<4, 64, 64, 4, 2>("tma f32 64x64 s4 o2"),
+        make_config<4, 64, 64, 3, 3>("tma f32 64x64 s3 o3"),
+        make_config<4, 32, 128, 4, 2>("tma f32 32x128 s4 o2"),
+        make_config<4, 128, 32, 4, 2>("tma f32 128x32 s4 o2"),
+        make_config<4, 64, 64, 6, 2>("tma f32 64x64 s6 o2"),
+        make_config<4, 32, 64, 6, 3>("tma f32 32x64 s6 o3"),
+    };
+    static const std::vector<TmaConfig> c2 = {
+        make_config<2, 64, 128, 4, 2>("tma 16b 64x128 s4 o2"),
+        make_config<2, 64, 128, 3, 3>("tma 16b 64x128 s3 o3"),
+        make_config<2, 128, 64, 4, 2>("tma 16b 128x64 s4 o2"),
+        make_config<2, 128, 128, 3, 2>("tma 16b 128x128 s3 o2"),
+        make_config<2, 64, 64, 6, 3>("tma 16b 64x64 s6 o3"),
+    };
     return esize == 4 ? c4 : c2;
 }
 
 size_t tma_smem_bytes(const TmaConfig &c)
 {
-    return size_t(c.stages + 2) * c.tile_bytes + size_t(c.stages) * 8;
+    return size_t(c.stages + c.nob) * c.tile_bytes + size_t(c.stages) * 16;
 }
+
+// Process-wide choice of TMA configuration per element size (autotuner).
+std::atomic<int> g_tma_choice[2] = {0, 0};
 
 // Per (device, config) launch facts: opt-in shared memory set, CTAs per SM.
 struct LaunchFacts {
@@ -255,14 +320,16 @@ struct LaunchFacts {
 };
 
 std::mutex g_facts_mu;
-LaunchFacts g_facts[64][2];
+std::map<std::pair<int, const void *>, LaunchFacts> g_facts;
 
 optigpu_status tma_launch_facts(const DeviceInfo &dev, const TmaConfig &c, int &ctas_per_sm)
 {
     std::lock_guard<std::mutex> lk(g_facts_mu);
-    LaunchFacts &f = g_facts[dev.device & 63][c.esize == 4 ? 0 : 1];
+    LaunchFacts &f = g_facts[{dev.device, c.fn}];
     if (!f.ready) {
         const size_t smem = tma_smem_bytes(c);
+        if (smem > dev.max_smem_optin)
+            return fail(OPTIGPU_ERR_INVALID_ARG, std::string("transpose config needs too much shared memory: ") + c.name);
         optigpu_status st = check_cuda(
             cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
             "cudaFuncSetAttribute(transpose tma smem)");
@@ -280,6 +347,9 @@ optigpu_status tma_launch_facts(const DeviceInfo &dev, const TmaConfig &c, int &
     return OPTIGPU_OK;
 }
 
+// Tile-rows per group of the TMA kernel's tile order.
+std::atomic<int> g_group_rows{16};
+
 bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, size_t esize)
 {
     if (esize != 2 && esize != 4)
@@ -296,13 +366,18 @@ bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, 
 }
 
 optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols, size_t esize,
-                          cudaStream_t stream)
+                          cudaStream_t stream, int config)
 {
     DeviceInfo dev;
     optigpu_status st = current_device(dev);
     if (st != OPTIGPU_OK)
         return st;
-    const TmaConfig &c = tma_config(esize);
+    const auto &configs = tma_configs(esize);
+    if (config < 0)
+        config = g_tma_choice[esize == 4 ? 0 : 1].load();
+    if (config < 0 || config >= int(configs.size()))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: unknown TMA configuration");
+    const TmaConfig &c = configs[size_t(config)];
     const CUtensorMapDataType type = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     alignas(64) CUtensorMap ms, md;
     // Source: dim0 = cols (contiguous), dim1 = rows; box TC x TR.
@@ -322,8 +397,9 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
     const int64_t grid = std::min<int64_t>(num_tiles, int64_t(ctas_per_sm) * dev.num_sms);
     const size_t smem = tma_smem_bytes(c);
     const uint64_t limit = wait_limit_ns();
-    int32_t tiles_c32 = int32_t(tiles_c);
-    void *args[] = {&ms, &md, &tiles_c32, const_cast<int64_t *>(&num_tiles), const_cast<uint64_t *>(&limit),
+    TileOrder order{int32_t(tiles_r), int32_t(tiles_c),
+                    std::max(1, std::min(g_group_rows.load(), int(tiles_r)))};
+    void *args[] = {&ms, &md, &order, const_cast<int64_t *>(&num_tiles), const_cast<uint64_t *>(&limit),
                     &dev.status_word};
     return check_cuda(cudaLaunchKernel(c.fn, dim3(unsigned(grid)), dim3(unsigned(c.threads)), args, smem, stream),
                       "launch transpose tma");
@@ -370,6 +446,40 @@ optigpu_status validate(const void *src, const void *dst, int64_t rows, int64_t 
 
 } // namespace
 
+// ------------------------------------------------------------- tuning hooks
+
+int transpose_num_configs(size_t esize) { return int(tma_configs(esize).size()) + 1; }
+
+const char *transpose_config_name(size_t esize, int config)
+{
+    const auto &c = tma_configs(esize);
+    if (config >= 0 && config < int(c.size()))
+        return c[size_t(config)].name;
+    if (config == int(c.size()))
+        return "tile32 padded 32x33 (no TMA)";
+    return nullptr;
+}
+
+int transpose_selected(size_t esize) { return g_tma_choice[esize == 4 ? 0 : 1].load(); }
+
+void transpose_select(size_t esize, int config) { g_tma_choice[esize == 4 ? 0 : 1].store(config); }
+
+void transpose_set_group_rows(int g) { g_group_rows.store(g > 0 ? g : 16); }
+
+int transpose_group_rows() { return g_group_rows.load(); }
+
+// Launches configuration `config` (an index of transpose_config_name) on an
+// eligible shape; the TMA configurations need tma_eligible().
+optigpu_status transpose_launch_config(const void *src, void *dst, int64_t rows, int64_t cols, size_t esize,
+                                       int config, cudaStream_t stream)
+{
+    if (config == int(tma_configs(esize).size()))
+        return launch_tile32(src, dst, rows, cols, esize, stream);
+    if (!tma_eligible(src, dst, rows, cols, esize))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: shape or alignment not eligible for TMA");
+    return launch_tma(src, dst, rows, cols, esize, stream, config);
+}
+
 optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype,
                                   int kernel, cudaStream_t stream)
 {
@@ -385,8 +495,11 @@ optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int6
     if (kernel == OPTIGPU_TRANSPOSE_TMA && !tma_ok)
         return fail(OPTIGPU_ERR_INVALID_ARG,
                     "transpose: TMA kernel needs 16-byte aligned pointers and rows, cols multiples of 16/esize");
-    if (kernel == OPTIGPU_TRANSPOSE_TMA || (kernel == OPTIGPU_TRANSPOSE_AUTO && tma_ok))
-        return launch_tma(src, dst, rows, cols, es, stream);
+    const int choice = transpose_selected(es);
+    if (kernel == OPTIGPU_TRANSPOSE_TMA)
+        return launch_tma(src, dst, rows, cols, es, stream, choice < int(tma_configs(es).size()) ? choice : 0);
+    if (kernel == OPTIGPU_TRANSPOSE_AUTO && tma_ok && choice < int(tma_configs(es).size()))
+        return launch_tma(src, dst, rows, cols, es, stream, choice);
     return launch_tile32(src, dst, rows, cols, es, stream);
 }
 

@@ -139,3 +139,31 @@ def test_roofline_workload_float32_16384():
 
 def test_precision_workload_bfloat16_8192():
     check(workloads.precision_matrix(), "bfloat16", "auto")
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+def test_every_compiled_configuration(dtype):
+    """Every configuration the autotuner may select is bit-exact, on shapes
+    with ragged last tiles in both directions."""
+    tdt = {"float32": torch.float32, "bfloat16": torch.bfloat16}[dtype]
+    names = api.tune_configs("transpose", tdt)
+    prev = api.tune_selected("transpose", tdt)
+    step = 16 // workloads.ESIZE[dtype]
+    shapes = [(step, step), (264, 136), (136, 264), (1000, 1024), (72, 4096)]
+    shapes = [(r - r % step or step, c - c % step or step) for r, c in shapes]
+    try:
+        for i, name in enumerate(names):
+            api.tune_select("transpose", tdt, i)
+            for r, c in shapes:
+                a = workloads.matrix(r, c, dtype, seed=r + 17 * c + i)
+                check(a, dtype, "auto")
+    finally:
+        api.tune_select("transpose", tdt, prev)
+
+
+def test_autotune_selects_a_valid_configuration():
+    idx, name, ms = api.autotune("transpose", torch.float32, 2048, 2048, reps=3)
+    assert 0 <= idx < len(api.tune_configs("transpose", torch.float32)) and ms > 0
+    a = workloads.matrix(2048, 2048, "float32", seed=8)
+    check(a, "float32", "auto")
+    api.tune_select("transpose", torch.float32, 0)
