@@ -144,6 +144,30 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
                                      optigpu_dtype dtype, void *out,
                                      uint32_t flags, optigpu_stream_t stream);
 
+/* Allocation-free sum.  The thesis has no counterpart to this entry point:
+ * it exists for callers that must not have the library allocate device
+ * memory -- applications that own all device memory through their own pool,
+ * loops that must not reach the driver's allocator after start-up, or
+ * processes held to a hard memory budget.
+ *   Same arguments, result and bit-identical summation order as
+ *   optigpu_reduce_sum_ex, but the per-chunk partials and the completion
+ *   counter live in one fixed device array of 256 KiB + 256 bytes that every
+ *   GPU loading the library holds until the process exits.  The call itself
+ *   allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ *   routine); it clears the counter with cudaMemsetAsync and launches.
+ *   n is limited to 32768 * OPTIGPU_REDUCE_CHUNK = 2^29 elements; larger n
+ *   returns INVALID_ARG with that limit in optigpu_last_error().
+ *   The first call on a device looks up the array's device address (set-up,
+ *   once per device, with that device current); make that first call before
+ *   any stream capture.
+ *   All calls share the one array: calls whose kernels overlap on the GPU
+ *   (for example on two streams at once) race and give wrong sums.  Order
+ *   them, e.g. by issuing them on one stream. */
+optigpu_status optigpu_reduce_sum_noalloc(const void *src, int64_t n,
+                                          optigpu_dtype dtype, void *out,
+                                          uint32_t flags,
+                                          optigpu_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Autotuning                                                               */
 /* ------------------------------------------------------------------------ */

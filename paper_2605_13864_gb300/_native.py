@@ -47,6 +47,7 @@ SIGNATURES = {
     "optigpu_transpose_tma_eligible": (_ci, [_vp, _vp, _i64, _i64, _ci]),
     "optigpu_reduce_sum": (_ci, [_vp, _i64, _ci, _vp, _vp]),
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
+    "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_tune_num_configs": (_ci, [_ci, _ci]),
     "optigpu_tune_config_name": (ctypes.c_char_p, [_ci, _ci, _ci]),
     "optigpu_tune_select": (_ci, [_ci, _ci, _ci]),

@@ -29,7 +29,9 @@
 // from run to run and between this entry point and the batched kernel.
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -189,3 +191,128 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n, optigpu_dtype d
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot let a library call cudaMalloc: a host application that
+// owns all device memory through its own pool and forbids side allocations,
+// a latency-critical loop that must not hit the driver's allocator (which can
+// synchronise the device) after start-up, or a process running close to a
+// hard device-memory budget.  optigpu_reduce_sum_noalloc serves them.  It
+// runs the same kernel as optigpu_reduce_sum_ex, but its partials and its
+// completion counter live in the fixed array below, which the CUDA runtime
+// places in every device's global memory when this module is loaded there,
+// and which stays there until the process exits.  The call itself allocates
+// nothing.  The first call on a device looks up the array's address (make it
+// before any stream capture).  All calls share the array, so calls whose
+// kernels overlap on the GPU race; the limit is 2^29 elements.
+// ---------------------------------------------------------------------------
+
+namespace optigpu {
+namespace {
+
+// Up to 32768 chunk partials (256 KiB): n <= 32768 * 16384 = 2^29 elements.
+constexpr int64_t kNoAllocMaxChunks = 32768;
+constexpr size_t kNoAllocScratchBytes = kReduceCounterBytes + size_t(kNoAllocMaxChunks) * 8;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+std::map<int, void *> g_noalloc_addr; // device -> device address of g_noalloc_scratch
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side handle, so the address is looked up
+// once per device, with that device current.
+optigpu_status noalloc_scratch(void **addr)
+{
+    int dev = -1;
+    optigpu_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != OPTIGPU_OK)
+        return st;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it == g_noalloc_addr.end()) {
+        void *p = nullptr;
+        if ((st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch),
+                             "cudaGetSymbolAddress(reduce scratch)")) != OPTIGPU_OK)
+            return st;
+        it = g_noalloc_addr.emplace(dev, p).first;
+    }
+    *addr = it->second;
+    return OPTIGPU_OK;
+}
+
+template <int DT, bool COMP>
+optigpu_status launch_noalloc(const void *src, int64_t n, void *out, cudaStream_t stream)
+{
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
+    if (num_chunks > kNoAllocMaxChunks)
+        return fail(OPTIGPU_ERR_INVALID_ARG,
+                    "reduce_sum_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
+                        std::to_string(kNoAllocMaxChunks * kReduceChunk) + " elements");
+    void *scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch)) != OPTIGPU_OK)
+        return st;
+    const void *fn = reinterpret_cast<const void *>(&reduce_sum_kernel<DT, COMP>);
+    int ctas_per_sm = 0;
+    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, fn, kReduceThreads, 0),
+                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(reduce)")) != OPTIGPU_OK)
+        return st;
+    unsigned *counter = static_cast<unsigned *>(scratch);
+    void *partials = static_cast<char *>(scratch) + kReduceCounterBytes;
+    // The array keeps whatever the previous call left; the counter must start
+    // at zero (the partials are all rewritten).
+    if ((st = check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), stream),
+                         "reduce_sum_noalloc: clear counter")) != OPTIGPU_OK)
+        return st;
+    const int64_t grid = std::min<int64_t>(num_chunks, int64_t(std::max(ctas_per_sm, 1)) * dev.num_sms);
+    const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
+    reduce_sum_kernel<DT, COMP><<<unsigned(grid), kReduceThreads, 0, stream>>>(src, n, vec_ok, partials, counter,
+                                                                             out, num_chunks);
+    return check_cuda(cudaGetLastError(), "launch reduce (noalloc)");
+}
+
+} // namespace
+} // namespace optigpu
+
+extern "C" optigpu_status optigpu_reduce_sum_noalloc(const void *src, int64_t n, optigpu_dtype dtype, void *out,
+                                                     uint32_t flags, optigpu_stream_t stream)
+{
+    using namespace optigpu;
+    const int dt = int(dtype);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!dtype_valid(dt))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce_sum_noalloc: unknown dtype " + std::to_string(dt));
+    if (flags & ~OPTIGPU_REDUCE_COMPENSATED)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_noalloc: unknown flag bits");
+    if (n < 0 || n > (int64_t(1) << 62))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_noalloc: n out of range");
+    if (!out || reinterpret_cast<uintptr_t>(out) % 8)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_noalloc: out must be a non-null 8-byte aligned pointer");
+    if (n > 0 && (!src || reinterpret_cast<uintptr_t>(src) % esize_of(dtype)))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_noalloc: src must be non-null and element-aligned");
+    if ((n + kReduceChunk - 1) / kReduceChunk > kNoAllocMaxChunks)
+        return fail(OPTIGPU_ERR_INVALID_ARG,
+                    "reduce_sum_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
+                        std::to_string(kNoAllocMaxChunks * kReduceChunk) + " elements");
+    if (n == 0)
+        return check_cuda(cudaMemsetAsync(out, 0, 8, s), "reduce_sum_noalloc: write 0");
+    const bool comp = (flags & OPTIGPU_REDUCE_COMPENSATED) != 0;
+    switch (dt) {
+    case OPTIGPU_INT32: return launch_noalloc<OPTIGPU_INT32, false>(src, n, out, s);
+    case OPTIGPU_FLOAT32:
+        return comp ? launch_noalloc<OPTIGPU_FLOAT32, true>(src, n, out, s)
+                    : launch_noalloc<OPTIGPU_FLOAT32, false>(src, n, out, s);
+    case OPTIGPU_BFLOAT16:
+        return comp ? launch_noalloc<OPTIGPU_BFLOAT16, true>(src, n, out, s)
+                    : launch_noalloc<OPTIGPU_BFLOAT16, false>(src, n, out, s);
+    default:
+        return comp ? launch_noalloc<OPTIGPU_FLOAT16, true>(src, n, out, s)
+                    : launch_noalloc<OPTIGPU_FLOAT16, false>(src, n, out, s);
+    }
+}
