@@ -85,7 +85,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -157,6 +157,172 @@ def cpu_baseline(seconds: float = 10.0):
     return {"value": round(done_bytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} x (transpose 4096x4096 fp32 + sum 2^24 fp32) in {dt:.1f} s, "
                       "plain C oracle, one host thread"}
+
+
+def measure_batched(steps: int = 10):
+    """The batched workload (4096 uneven instances, seed 3) as one persistent
+    CUDA-graph launch, against the same 4096 instances issued as separate
+    plain calls on one stream (from Python, and replayed from a CUDA graph)."""
+    import torch
+    from paper_2605_13864_gb300 import api, workloads
+
+    inst = workloads.batched_instances()
+    data = workloads.batched_data(inst)
+    tdt = {"float32": torch.float32}
+    items = []
+    for i, a in zip(inst, data):
+        d = torch.from_numpy(a).cuda()
+        if i.op == 0:
+            items.append(("transpose", d, torch.empty((i.cols, i.rows), dtype=tdt[i.dtype], device="cuda")))
+        else:
+            items.append(("reduce", d, torch.empty((), dtype=torch.float64, device="cuda")))
+    del data
+    plan = api.BatchPlan(items)
+    best = plan.autotune(reps=3)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n, (time.perf_counter() - t0) * 1e3 / n
+
+    batch_ms, batch_wall = timed(plan.run, steps)
+
+    def separate():
+        for op, d, o in items:
+            if op == "transpose":
+                api.transpose(d, out=o)
+            else:
+                api.reduce_sum(d, out=o)
+
+    sep_ms, sep_wall = timed(separate, 2)
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    api.reduce_reserve(max(i.rows for i in inst if i.op == 1), stream=cap)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=cap):
+        separate()
+    sep_graph_ms, _ = timed(g.replay, 3)
+    n = len(inst)
+    res = {
+        "workload": "4096 instances: 2048 fp32 transposes rows,cols log-uniform [1,2048] + "
+                    "2048 fp32 sums n log-uniform [1,2^22], seed 3",
+        "algorithmic_bytes": info["bytes"], "items": info["items"], "grid": info["grid"],
+        "config": best[1],
+        "batched_ms": round(batch_ms, 4), "batched_gbs": round(info["bytes"] / batch_ms / 1e6, 1),
+        "batched_instances_per_s": round(n / batch_ms * 1e3, 1),
+        "separate_launches_ms": round(sep_ms, 4), "separate_launches_wall_ms": round(sep_wall, 3),
+        "separate_launches_graph_ms": round(sep_graph_ms, 4),
+        "speedup_vs_separate": round(sep_ms / batch_ms, 2),
+        "speedup_vs_separate_graph": round(sep_graph_ms / batch_ms, 2),
+        "launches_per_run": 1,
+    }
+    plan.close()
+    del items, g
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: int = 400):
+    """The serving workload: an open-loop Poisson stream of `count` requests
+    at `rate` req/s (seed 4; op 50/50, dtype uniform over int32/fp32/bf16,
+    sizes as in the batched workload) served under a 40 GB device budget by
+    the continuous-batching server and by the per-call baseline; then both at
+    saturation (every request queued at t = 0).  Inputs come from pinned host
+    payload pools (one per dtype); every sum and a sample of transposes are
+    checked against the CPU oracle."""
+    import torch
+    import oracle
+    from paper_2605_13864_gb300 import api, workloads
+
+    reqs = workloads.serving_requests(count=count, rate=rate, seed=4)
+    rng = np.random.default_rng(40)
+    pool_elems = 1 << 23  # 8 Mi elements per dtype (>= the largest request, 4,194,304)
+    pools = {
+        "int32": torch.from_numpy(rng.integers(-1000, 1001, pool_elems, dtype=np.int32)).pin_memory(),
+        "float32": torch.from_numpy(rng.standard_normal(pool_elems, dtype=np.float32)).pin_memory(),
+        "bfloat16": torch.from_numpy(rng.standard_normal(pool_elems, dtype=np.float32)).to(torch.bfloat16).pin_memory(),
+    }
+    out_ring = torch.empty(1 << 28, dtype=torch.uint8).pin_memory()  # 256 MiB of transpose outputs
+    sums = torch.empty(count, dtype=torch.float64).pin_memory()
+    sample = set(rng.choice(count, size=min(check_sample, count), replace=False).tolist())
+    esize = {"int32": 4, "float32": 4, "bfloat16": 2}
+    host, checks = [], []
+    ring = 0
+    for k, r in enumerate(reqs):
+        i = r.inst
+        n = i.rows * i.cols
+        off = int((k * 2654435761) % (pool_elems - n + 1)) & ~7
+        src = pools[i.dtype][off:off + n]
+        if i.op == 0:
+            src = src.view(i.rows, i.cols)
+            nbytes = n * esize[i.dtype]
+            if k in sample:
+                dst = torch.empty((i.cols, i.rows), dtype=src.dtype).pin_memory()
+                checks.append((k, "transpose", src, dst))
+            else:
+                if ring + nbytes > out_ring.numel():
+                    ring = 0
+                dst = out_ring[ring:ring + nbytes].view(src.dtype).view(i.cols, i.rows)
+                ring = (ring + nbytes + 255) & ~255
+            host.append(("transpose", src, dst))
+        else:
+            dst = sums[k:k + 1].view(()) if i.dtype != "int32" else sums[k:k + 1].view(torch.int64).view(())
+            host.append(("reduce", src, dst))
+            if k in sample:
+                checks.append((k, "reduce", src, dst))
+    arrivals = np.array([r.arrival_s for r in reqs])
+    res = {"workload": f"{count} requests, Poisson {rate:.0f} req/s, op 50/50, dtype int32/fp32/bf16, "
+                       "sizes log-uniform (transpose sides [1,2048], sum n [1,2^22]), seed 4, budget 40 GB"}
+    for mode, per_call, streams in (("batched", False, 4), ("per_call", True, 32)):
+        sv = api.Server(budget_bytes=40 << 30, max_slots=256, n_streams=streams, per_call=per_call)
+        sv.replay(host[:2000], arrivals[:2000] * 0)  # warm-up: kernels loaded, workspaces sized
+        t0 = time.perf_counter()
+        lat = sv.replay(host, arrivals)
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+        t1 = time.perf_counter()
+        sat_n = min(count, 20_000)
+        sv.replay(host[:sat_n], np.zeros(sat_n))
+        sat = time.perf_counter() - t1
+        res[mode] = {"req_per_s": round(count / wall, 1), "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 4),
+                     "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 4),
+                     "mean_ms": round(float(lat.mean()) * 1e3, 4),
+                     "saturated_req_per_s": round(sat_n / sat, 1),
+                     "steps": st["steps"], "kernel_launches": st["launches"],
+                     "max_in_flight": st["max_in_flight"], "peak_device_bytes": st["peak_bytes"],
+                     "streams": streams}
+        sv.close()
+    # Exactness: every sum, a sample of transposes (results of the last run).
+    ok = bad = 0
+    for k, op, src, dst in checks:
+        dt = reqs[k].inst.dtype
+        a = src.numpy() if dt != "bfloat16" else src.view(torch.int16).numpy().view(np.uint16)
+        if op == "transpose":
+            got = dst.numpy() if dt != "bfloat16" else dst.view(torch.int16).numpy().view(np.uint16)
+            good = np.array_equal(got.view(np.uint8), oracle.transpose(a).view(np.uint8))
+        elif dt == "int32":
+            good = int(dst.view(torch.int64).item()) == oracle.sum_i64(a)
+        else:
+            ref = oracle.reduce_reference(a, dt)
+            good = abs(float(dst.item()) - ref["f64"]) <= 1e-6 * ref["abs"] + 1e-300
+        ok += int(good)
+        bad += int(not good)
+    res["checked"] = {"requests": ok + bad, "exact_or_within_tol": ok, "failed": bad,
+                      "what": f"{check_sample} sampled requests (sums and transposes) against the CPU oracle"}
+    b, c = res["batched"], res["per_call"]
+    res["batched_vs_per_call"] = {"saturated_req_per_s_ratio": round(b["saturated_req_per_s"] / c["saturated_req_per_s"], 2),
+                                  "p99_ratio": round(b["p99_ms"] / c["p99_ms"], 3)}
+    return res
 
 
 def run_reference(args):
@@ -311,6 +477,10 @@ def run_gpu(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if not args.no_batched:
+            line["batched"] = measure_batched()
+        if not args.no_served:
+            line["served"] = measure_served()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -323,11 +493,13 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["optigpu", "reference"], default="optigpu")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -68,6 +68,13 @@ typedef enum {
     OPTIGPU_ERR_NOT_FOUND = 8         /* unknown ticket or handle */
 } optigpu_status;
 
+/* Operations, for batch descriptors and the autotuner. */
+typedef enum {
+    OPTIGPU_OP_TRANSPOSE = 0,
+    OPTIGPU_OP_REDUCE = 1,
+    OPTIGPU_OP_BATCH = 2 /* autotuner only: the batch kernel's configurations */
+} optigpu_op;
+
 /* ------------------------------------------------------------------------ */
 /* Transpose (Listing 3.5, Sec. 3.1)                                        */
 /* ------------------------------------------------------------------------ */
@@ -144,6 +151,12 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
                                      optigpu_dtype dtype, void *out,
                                      uint32_t flags, optigpu_stream_t stream);
 
+/* Allocates (or grows) the workspace `stream` needs for sums of up to n
+ * elements, so that later sums on that stream -- for example inside a CUDA
+ * graph capture -- allocate nothing.  INVALID_ARG for n < 0, OOM on
+ * allocation failure. */
+optigpu_status optigpu_reduce_reserve(int64_t n, optigpu_stream_t stream);
+
 /* Allocation-free sum.  The thesis has no counterpart to this entry point:
  * it exists for callers that must not have the library allocate device
  * memory -- applications that own all device memory through their own pool,
@@ -169,6 +182,142 @@ optigpu_status optigpu_reduce_sum_noalloc(const void *src, int64_t n,
                                           optigpu_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many uneven transposes and sums in one persistent launch        */
+/* ------------------------------------------------------------------------ */
+/* The thesis launches one kernel per problem (Listings 3.6, 6.21).  A batch
+ * plan runs thousands of independent instances of both problems in one
+ * persistent kernel fed by a device work queue (an integer atomic counter).
+ * Each instance computes exactly what the single calls compute: transposes
+ * are bit copies and every sum is bit-identical to optigpu_reduce_sum_ex with
+ * the same flags (same chunks, same combine order), whatever the mix. */
+
+/* One instance of a batch. */
+typedef struct {
+    int32_t op;      /* OPTIGPU_OP_TRANSPOSE or OPTIGPU_OP_REDUCE */
+    int32_t dtype;   /* optigpu_dtype */
+    const void *src; /* device input: rows x cols (transpose) or rows elements (sum) */
+    void *dst;       /* transpose: cols x rows output; sum: the 8-byte result (int64 or double) */
+    int64_t rows;    /* transpose rows, or the sum's length n */
+    int64_t cols;    /* transpose cols; ignored for sums */
+} optigpu_desc;
+
+typedef struct optigpu_batch_plan optigpu_batch_plan;
+
+/* Plan flags (OPTIGPU_REDUCE_COMPENSATED applies to every float sum). */
+#define OPTIGPU_BATCH_NO_GRAPH 2u /* launch directly instead of replaying a CUDA graph */
+
+/* Validates the `count` descriptors, flattens them into work items (tiles of
+ * the transposes, 16384-element chunks of the sums), uploads the tables to a
+ * plan-owned device workspace (cudaMalloc; freed by _destroy) and captures
+ * one run -- queue reset and kernel launch -- into a CUDA graph.  Every
+ * descriptor is checked like the single calls (INVALID_ARG,
+ * UNSUPPORTED_DTYPE, OVERLAP within an instance).  Instances must not write
+ * to memory that another instance of the plan reads or writes.  The plan
+ * keeps the pointers: the buffers must stay valid while it is used.
+ * Synchronous; must not run during stream capture. */
+optigpu_status optigpu_batch_plan_create(const optigpu_desc *descs, int32_t count,
+                                         uint32_t flags, optigpu_batch_plan **plan);
+
+/* Enqueues one run of the plan on `stream` (one graph launch).  Runs of one
+ * plan share its workspace: order them (one stream, or events). */
+optigpu_status optigpu_batch_run(optigpu_batch_plan *plan, optigpu_stream_t stream);
+
+/* Work items, algorithmic bytes of one run (2*esize*rows*cols per
+ * transpose, esize*n per sum) and persistent grid size of the last run. */
+optigpu_status optigpu_batch_plan_info(const optigpu_batch_plan *plan, int64_t *items,
+                                       int64_t *bytes, int32_t *grid);
+
+/* Times every batch configuration (transpose tile 32 or 64, CTAs per SM) on
+ * this plan's own buffers -- the instances are really computed, so outputs
+ * are overwritten with the same values -- selects the fastest for the plan
+ * and as the default of later plans, and re-captures the graph.
+ * Synchronises `stream`. */
+optigpu_status optigpu_batch_autotune(optigpu_batch_plan *plan, int reps,
+                                      optigpu_stream_t stream, int *best_config,
+                                      float *best_ms);
+
+/* Frees the plan's workspace and graph (wait for its runs first). */
+void optigpu_batch_plan_destroy(optigpu_batch_plan *plan);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of transpose and sum requests               */
+/* ------------------------------------------------------------------------ */
+/* The thesis runs each problem once from host code (Listings 3.6, 3.11:
+ * allocate, copy in, launch, copy out, free).  The server keeps that flow per
+ * request but shares the device among many requests: it admits queued
+ * requests while slots and a device-memory budget allow, keeps their buffers
+ * in a device arena, copies their inputs in, runs each step's admitted
+ * requests as one persistent batch kernel (the batch plans' kernel), copies
+ * results out and frees the buffers when the step's completion event fires.
+ * Requests that arrive while earlier steps run go into the next step on
+ * another stream, so their copies and kernels overlap on the device.  Each
+ * result equals the single call's (transposes bit for bit, sums bit-identical
+ * to optigpu_reduce_sum_ex with the server's flags). */
+
+typedef struct optigpu_server optigpu_server;
+
+/* One request: the data lives in HOST memory (pinned memory makes the copies
+ * asynchronous).  host_dst receives cols x rows elements for a transpose, or
+ * one 8-byte value (int64 / double) for a sum.  Both buffers must stay valid
+ * until the request is done. */
+typedef struct {
+    int32_t op;           /* OPTIGPU_OP_TRANSPOSE or OPTIGPU_OP_REDUCE */
+    int32_t dtype;        /* optigpu_dtype */
+    int64_t rows;         /* transpose rows, or the sum's length n */
+    int64_t cols;         /* transpose cols; ignored for sums */
+    const void *host_src; /* rows x cols (or n) elements */
+    void *host_dst;
+} optigpu_request;
+
+typedef struct {
+    int64_t submitted, completed, pending, in_flight, max_in_flight;
+    int64_t steps;    /* launched steps (stream submissions) */
+    int64_t launches; /* kernel launches (1 per batched step; 1 per request in per-call mode) */
+    int64_t bytes_in_use, peak_bytes; /* device arena */
+} optigpu_server_stats;
+
+/* Server flags (OPTIGPU_REDUCE_COMPENSATED applies to every float sum). */
+#define OPTIGPU_SERVER_PER_CALL 4u /* baseline: one plain kernel per request, one request per stream */
+
+/* Creates a server with a device arena of mem_budget_bytes (one cudaMalloc,
+ * >= 1 MiB), at most max_slots requests on the device at once and n_streams
+ * streams (1..1024; at most n_streams steps in flight).  INVALID_ARG for bad
+ * sizes or flags, OOM if the budget cannot be allocated. */
+optigpu_status optigpu_server_create(size_t mem_budget_bytes, int32_t max_slots,
+                                     int32_t n_streams, uint32_t flags,
+                                     optigpu_server **server);
+
+/* Queues a request (validated now: INVALID_ARG / UNSUPPORTED_DTYPE, or
+ * INVALID_ARG if it alone exceeds the budget); returns its ticket.  BUSY
+ * when the queue holds 2^24 requests. */
+optigpu_status optigpu_server_submit(optigpu_server *server, const optigpu_request *req,
+                                     uint64_t *ticket);
+
+/* One round of the loop: completes finished steps, admits queued requests in
+ * arrival order into every free stream while slots and budget allow, and
+ * launches them.  *launched (may be NULL) = number of steps launched. */
+optigpu_status optigpu_server_step(optigpu_server *server, int32_t *launched);
+
+/* *done = 1 once the ticket's result is in its host buffer (the ticket is
+ * then forgotten); NOT_FOUND for unknown or already-reported tickets. */
+optigpu_status optigpu_server_poll(optigpu_server *server, uint64_t ticket, int32_t *done);
+
+/* Steps until every queued request has completed. */
+optigpu_status optigpu_server_drain(optigpu_server *server);
+
+optigpu_status optigpu_server_get_stats(optigpu_server *server, optigpu_server_stats *stats);
+
+/* Replays an open-loop trace: request i is submitted when arrival_s[i]
+ * seconds (non-decreasing) have passed since the call started; the loop
+ * steps until all have completed and writes latency_s[i] = completion time
+ * (the host sees the step's event fire) - arrival time. */
+optigpu_status optigpu_server_replay(optigpu_server *server, const optigpu_request *reqs,
+                                     const double *arrival_s, int64_t count, double *latency_s);
+
+/* Waits for the server's streams and frees everything it owns. */
+void optigpu_server_destroy(optigpu_server *server);
+
+/* ------------------------------------------------------------------------ */
 /* Autotuning                                                               */
 /* ------------------------------------------------------------------------ */
 /* The thesis fixes its launch parameters by hand (the tile size 32 and the
@@ -178,13 +327,12 @@ optigpu_status optigpu_reduce_sum_noalloc(const void *src, int64_t n,
  * them by measurement.  Selections are process-wide.  None of them changes a
  * result: transposes are bit copies and the sum's chunk partition is fixed. */
 
-typedef enum {
-    OPTIGPU_OP_TRANSPOSE = 0,
-    OPTIGPU_OP_REDUCE = 1
-} optigpu_op;
+
 
 /* Number of configurations of `op` for `dtype` (-1 for a bad op or dtype).
- * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel. */
+ * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel.
+ * OPTIGPU_OP_BATCH ignores `dtype`; its selection is the default of new
+ * plans. */
 int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype);
 
 /* Static name of configuration `config`, or NULL if out of range. */

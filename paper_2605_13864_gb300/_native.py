@@ -48,6 +48,22 @@ SIGNATURES = {
     "optigpu_reduce_sum": (_ci, [_vp, _i64, _ci, _vp, _vp]),
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
+    "optigpu_reduce_reserve": (_ci, [_i64, _vp]),
+    "optigpu_batch_plan_create": (_ci, [_vp, ctypes.c_int32, _u32, ctypes.POINTER(_vp)]),
+    "optigpu_batch_run": (_ci, [_vp, _vp]),
+    "optigpu_batch_plan_info": (_ci, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "optigpu_batch_autotune": (_ci, [_vp, _ci, _vp, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_float)]),
+    "optigpu_batch_plan_destroy": (None, [_vp]),
+    "optigpu_server_create": (_ci, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, _u32,
+                                    ctypes.POINTER(_vp)]),
+    "optigpu_server_submit": (_ci, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "optigpu_server_step": (_ci, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "optigpu_server_poll": (_ci, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]),
+    "optigpu_server_drain": (_ci, [_vp]),
+    "optigpu_server_get_stats": (_ci, [_vp, _vp]),
+    "optigpu_server_replay": (_ci, [_vp, _vp, _vp, _i64, _vp]),
+    "optigpu_server_destroy": (None, [_vp]),
     "optigpu_tune_num_configs": (_ci, [_ci, _ci]),
     "optigpu_tune_config_name": (ctypes.c_char_p, [_ci, _ci, _ci]),
     "optigpu_tune_select": (_ci, [_ci, _ci, _ci]),
@@ -65,6 +81,29 @@ SIGNATURES = {
     "optigpu_release_workspaces": (_ci, []),
     "optigpu_version": (_ci, []),
 }
+
+
+class Desc(ctypes.Structure):
+    """optigpu_desc: one instance of a batch."""
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32), ("src", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    """optigpu_request: one served request with host buffers."""
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("host_src", ctypes.c_void_p), ("host_dst", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "pending", "in_flight",
+                                               "max_in_flight", "steps", "launches", "bytes_in_use",
+                                               "peak_bytes")]
+
+
+SERVER_PER_CALL = 4
+BATCH_NO_GRAPH = 2
+OP_BATCH = 2
 
 
 class OptigpuError(RuntimeError):

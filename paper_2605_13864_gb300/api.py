@@ -82,6 +82,12 @@ def reduce_sum(x: torch.Tensor, compensated: bool = False, out: torch.Tensor | N
     return out
 
 
+def reduce_reserve(n: int, stream=None) -> None:
+    """Pre-allocates the sum workspace of ``stream`` for up to ``n`` elements
+    (do this before capturing sums into a CUDA graph)."""
+    N.check(N.lib().optigpu_reduce_reserve(int(n), _stream_ptr(stream)), "optigpu_reduce_reserve")
+
+
 def tma_eligible(src: torch.Tensor, dst: torch.Tensor) -> bool:
     rows, cols = src.shape
     return bool(N.lib().optigpu_transpose_tma_eligible(src.data_ptr(), dst.data_ptr(), rows, cols,
@@ -103,10 +109,10 @@ def release_workspaces() -> None:
 
 # ---------------------------------------------------------------- autotuning
 
-_OPS = {"transpose": N.OP_TRANSPOSE, "reduce": N.OP_REDUCE}
+_OPS = {"transpose": N.OP_TRANSPOSE, "reduce": N.OP_REDUCE, "batch": N.OP_BATCH}
 
 
-def tune_configs(op: str, dtype: torch.dtype) -> list[str]:
+def tune_configs(op: str, dtype: torch.dtype = torch.float32) -> list[str]:
     """Names of the compiled configurations of ``op`` for ``dtype``."""
     L = N.lib()
     n = L.optigpu_tune_num_configs(_OPS[op], dtype_code(dtype))
@@ -143,3 +149,177 @@ def tune_save(path: str) -> None:
 
 def tune_load(path: str) -> None:
     N.check(N.lib().optigpu_tune_load(path.encode()), "optigpu_tune_load")
+
+
+# ------------------------------------------------------------------ batches
+
+class BatchPlan:
+    """Many transposes and sums in one persistent launch (optigpu_batch_*).
+
+    ``items`` is a list of ``("transpose", src, dst)`` or
+    ``("reduce", src, out)`` with CUDA tensors (``dst`` is cols x rows,
+    ``out`` a 0-d int64 / float64 tensor).  The plan keeps references to the
+    tensors so their memory stays valid while the plan lives.
+    """
+
+    def __init__(self, items, compensated: bool = False, graph: bool = True):
+        import ctypes
+        self._keep = []
+        descs = (N.Desc * max(len(items), 1))()
+        for k, (op, src, dst) in enumerate(items):
+            d = descs[k]
+            d.dtype = dtype_code(src.dtype)
+            d.src = src.data_ptr() if src.numel() else None
+            d.dst = dst.data_ptr() if dst.numel() else None
+            if op == "transpose":
+                d.op = N.OP_TRANSPOSE
+                d.rows, d.cols = int(src.shape[0]), int(src.shape[1])
+                if not (src.is_contiguous() and dst.is_contiguous()) or tuple(dst.shape) != (d.cols, d.rows):
+                    raise ValueError(f"batch item {k}: contiguous src (r, c) and dst (c, r) required")
+            elif op == "reduce":
+                d.op = N.OP_REDUCE
+                d.rows, d.cols = int(src.numel()), 1
+                want = torch.int64 if src.dtype == torch.int32 else torch.float64
+                if dst.dtype != want or dst.numel() != 1:
+                    raise ValueError(f"batch item {k}: out must hold one {want}")
+            else:
+                raise ValueError(f"batch item {k}: unknown op {op!r}")
+            self._keep.append((src, dst))
+        flags = (N.REDUCE_COMPENSATED if compensated else 0) | (0 if graph else N.BATCH_NO_GRAPH)
+        plan = ctypes.c_void_p()
+        N.check(N.lib().optigpu_batch_plan_create(descs, len(items), flags, ctypes.byref(plan)),
+                "optigpu_batch_plan_create")
+        self._plan = plan
+
+    def run(self, stream=None) -> None:
+        N.check(N.lib().optigpu_batch_run(self._plan, _stream_ptr(stream)), "optigpu_batch_run")
+
+    def info(self) -> dict:
+        import ctypes
+        items, nbytes, grid = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        N.check(N.lib().optigpu_batch_plan_info(self._plan, ctypes.byref(items), ctypes.byref(nbytes),
+                                                ctypes.byref(grid)), "optigpu_batch_plan_info")
+        return {"items": items.value, "bytes": nbytes.value, "grid": grid.value}
+
+    def autotune(self, reps: int = 5, stream=None):
+        import ctypes
+        best, ms = ctypes.c_int(-1), ctypes.c_float()
+        N.check(N.lib().optigpu_batch_autotune(self._plan, int(reps), _stream_ptr(stream), ctypes.byref(best),
+                                               ctypes.byref(ms)), "optigpu_batch_autotune")
+        return best.value, tune_configs("batch")[best.value], float(ms.value)
+
+    def close(self) -> None:
+        if getattr(self, "_plan", None) is not None and self._plan.value:
+            torch.cuda.synchronize()
+            N.lib().optigpu_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def _host_request(op: str, src: torch.Tensor, dst: torch.Tensor) -> "N.Request":
+    r = N.Request()
+    r.dtype = dtype_code(src.dtype)
+    if src.is_cuda or dst.is_cuda:
+        raise ValueError("served requests carry host (CPU) tensors")
+    if op == "transpose":
+        r.op = N.OP_TRANSPOSE
+        r.rows, r.cols = int(src.shape[0]), int(src.shape[1])
+        if tuple(dst.shape) != (r.cols, r.rows) or not dst.is_contiguous():
+            raise ValueError("dst must be a contiguous (cols, rows) tensor")
+    elif op == "reduce":
+        r.op = N.OP_REDUCE
+        r.rows, r.cols = int(src.numel()), 1
+        want = torch.int64 if src.dtype == torch.int32 else torch.float64
+        if dst.dtype != want or dst.numel() != 1:
+            raise ValueError(f"out must hold one {want}")
+    else:
+        raise ValueError(f"unknown op {op!r}")
+    if not src.is_contiguous():
+        raise ValueError("src must be contiguous")
+    r.host_src = src.data_ptr() if src.numel() else None
+    r.host_dst = dst.data_ptr()
+    return r
+
+
+class Server:
+    """Continuous-batching server (optigpu_server_*) over host tensors.
+
+    Pinned host tensors (``tensor.pin_memory()``) make the copies
+    asynchronous.  ``per_call=True`` is the baseline that launches one plain
+    kernel per request.
+    """
+
+    def __init__(self, budget_bytes: int = 1 << 30, max_slots: int = 256, n_streams: int = 4,
+                 per_call: bool = False, compensated: bool = False):
+        import ctypes
+        flags = (N.SERVER_PER_CALL if per_call else 0) | (N.REDUCE_COMPENSATED if compensated else 0)
+        h = ctypes.c_void_p()
+        N.check(N.lib().optigpu_server_create(int(budget_bytes), int(max_slots), int(n_streams), flags,
+                                              ctypes.byref(h)), "optigpu_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, op: str, src: torch.Tensor, dst: torch.Tensor) -> int:
+        import ctypes
+        r = _host_request(op, src, dst)
+        tk = ctypes.c_uint64()
+        N.check(N.lib().optigpu_server_submit(self._h, ctypes.byref(r), ctypes.byref(tk)), "optigpu_server_submit")
+        self._keep[tk.value] = (src, dst)
+        return tk.value
+
+    def step(self) -> int:
+        import ctypes
+        n = ctypes.c_int32()
+        N.check(N.lib().optigpu_server_step(self._h, ctypes.byref(n)), "optigpu_server_step")
+        return n.value
+
+    def poll(self, ticket: int) -> bool:
+        import ctypes
+        d = ctypes.c_int32()
+        N.check(N.lib().optigpu_server_poll(self._h, int(ticket), ctypes.byref(d)), "optigpu_server_poll")
+        if d.value:
+            self._keep.pop(ticket, None)
+        return bool(d.value)
+
+    def drain(self) -> None:
+        N.check(N.lib().optigpu_server_drain(self._h), "optigpu_server_drain")
+
+    def stats(self) -> dict:
+        import ctypes
+        st = N.ServerStats()
+        N.check(N.lib().optigpu_server_get_stats(self._h, ctypes.byref(st)), "optigpu_server_get_stats")
+        return {name: getattr(st, name) for name, _ in N.ServerStats._fields_}
+
+    def replay(self, requests, arrivals_s):
+        """Open-loop replay of ``requests`` (list of (op, src, dst) host
+        tensors) at ``arrivals_s`` seconds; returns per-request latencies (s)."""
+        import ctypes
+        import numpy as np
+        n = len(requests)
+        arr = (N.Request * max(n, 1))()
+        for i, (op, src, dst) in enumerate(requests):
+            arr[i] = _host_request(op, src, dst)
+        t = np.ascontiguousarray(arrivals_s, dtype=np.float64)
+        lat = np.zeros(n, dtype=np.float64)
+        N.check(N.lib().optigpu_server_replay(self._h, ctypes.cast(arr, ctypes.c_void_p), t.ctypes.data, n,
+                                              lat.ctypes.data), "optigpu_server_replay")
+        return lat
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().optigpu_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,599 @@
+// batch.cu -- many uneven transposes and sums in one persistent launch.
+//
+// A plan flattens a descriptor table into work items: a transpose of
+// rows x cols becomes ceil(rows/TILE) * ceil(cols/TILE) tile items, a sum of
+// n elements becomes ceil(n / 16384) chunk items (the same chunks as the
+// single-call sum).  A persistent grid (CTAs per SM x SMs) pulls items from a
+// device work queue -- one integer atomic counter, each CTA claiming its next
+// item while it works on the current one.  A chunk item writes its partial to
+// the instance's slot and bumps the instance's completion counter; the CTA
+// that finishes an instance's last chunk runs that instance's fixed-order
+// FP64 / int64 final combine and resets the counter.  No float atomics; every
+// sum is bit-identical to the single-call result, and every transpose is a
+// bit copy, whatever the batch mix and the grid size.
+//
+// The plan owns its device workspace and a CUDA graph of one run (queue
+// reset + kernel launch), so a run is one cudaGraphLaunch.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "batch_core.h"
+#include "internal.h"
+#include "reduce_core.cuh"
+
+namespace optigpu {
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+
+template <int TILE>
+struct BatchShared {
+    union {
+        uint32_t t32[TILE][TILE + 1];
+        uint16_t t16[TILE][TILE + 2];
+        ReduceCore<OPTIGPU_INT32, false>::Shared ri;
+        ReduceCore<OPTIGPU_FLOAT32, false>::Shared rf;
+        ReduceCore<OPTIGPU_FLOAT32, true>::Shared rfc;
+        ReduceCore<OPTIGPU_BFLOAT16, false>::Shared rb;
+        ReduceCore<OPTIGPU_BFLOAT16, true>::Shared rbc;
+        ReduceCore<OPTIGPU_FLOAT16, false>::Shared rh;
+        ReduceCore<OPTIGPU_FLOAT16, true>::Shared rhc;
+    } u;
+    BatchInst desc[2];
+    int64_t item[2];
+    int last;
+};
+
+// One TILE x TILE tile of a transpose: coalesced row reads into a padded
+// shared tile, coalesced row writes of its columns.  Edges are predicated.
+template <int TILE, typename T, typename Tile>
+__device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t local, Tile &tile)
+{
+    constexpr int ROWS_PER_PASS = kBatchThreads / TILE;
+    const T *src = static_cast<const T *>(in.src);
+    T *dst = static_cast<T *>(in.dst);
+    const int64_t tr = local / in.aux, tc = local - (local / in.aux) * in.aux;
+    const int64_t r0 = tr * TILE, c0 = tc * TILE;
+    const int x = threadIdx.x % TILE, y0 = threadIdx.x / TILE;
+    const int64_t rows = in.rows, cols = in.cols;
+#pragma unroll
+    for (int j = 0; j < TILE; j += ROWS_PER_PASS) {
+        const int64_t r = r0 + y0 + j, c = c0 + x;
+        if (r < rows && c < cols)
+            tile[y0 + j][x] = src[r * cols + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < TILE; j += ROWS_PER_PASS) {
+        const int64_t orow = c0 + y0 + j, ocol = r0 + x;
+        if (orow < cols && ocol < rows)
+            dst[orow * rows + ocol] = tile[x][y0 + j];
+    }
+}
+
+template <int DT, bool COMP, typename Sh>
+__device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local, uint32_t inst, void *partials,
+                                             unsigned *inst_done, Sh &sh, int &s_last)
+{
+    using Core = ReduceCore<DT, COMP>;
+    using P = typename Core::Partial;
+    auto &rs = *reinterpret_cast<typename Core::Shared *>(&sh);
+    P *mine = static_cast<P *>(partials) + in.aux;
+    const P part = Core::chunk_partial(in.src, in.rows, local, in.vec_ok != 0, rs);
+    if (threadIdx.x == 0) {
+        mine[local] = part;
+        __threadfence();
+        s_last = (atomicAdd(inst_done + inst, 1u) == unsigned(in.nitems) - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        Core::final_combine(mine, in.nitems, in.dst, rs);
+        if (threadIdx.x == 0)
+            inst_done[inst] = 0u;
+    }
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(kBatchThreads)
+batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ item_inst, int64_t total_items,
+             unsigned long long *queue, unsigned *inst_done, void *partials, int compensated)
+{
+    __shared__ BatchShared<TILE> sh;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const int64_t it = int64_t(atomicAdd(queue, 1ull));
+        sh.item[0] = it;
+        if (it < total_items)
+            sh.desc[0] = insts[item_inst[it]];
+    }
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const int64_t item = sh.item[cur];
+        if (item >= total_items)
+            break;
+        int64_t next = 0;
+        if (t == 0)
+            next = int64_t(atomicAdd(queue, 1ull)); // claim ahead, used after this item
+        const BatchInst in = sh.desc[cur];
+        const uint32_t inst = item_inst[item];
+        const int64_t local = item - in.first_item;
+        if (in.op == OPTIGPU_OP_TRANSPOSE) {
+            if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
+                transpose_tile<TILE, uint16_t>(in, local, sh.u.t16);
+            else
+                transpose_tile<TILE, uint32_t>(in, local, sh.u.t32);
+        } else {
+            switch (in.dtype * 2 + (compensated ? 1 : 0)) {
+            case OPTIGPU_INT32 * 2:
+            case OPTIGPU_INT32 * 2 + 1:
+                reduce_chunk<OPTIGPU_INT32, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            case OPTIGPU_FLOAT32 * 2:
+                reduce_chunk<OPTIGPU_FLOAT32, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            case OPTIGPU_FLOAT32 * 2 + 1:
+                reduce_chunk<OPTIGPU_FLOAT32, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            case OPTIGPU_BFLOAT16 * 2:
+                reduce_chunk<OPTIGPU_BFLOAT16, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            case OPTIGPU_BFLOAT16 * 2 + 1:
+                reduce_chunk<OPTIGPU_BFLOAT16, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            case OPTIGPU_FLOAT16 * 2:
+                reduce_chunk<OPTIGPU_FLOAT16, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            default:
+                reduce_chunk<OPTIGPU_FLOAT16, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                break;
+            }
+        }
+        if (t == 0) {
+            sh.item[cur ^ 1] = next;
+            if (next < total_items)
+                sh.desc[cur ^ 1] = insts[item_inst[next]];
+        }
+        __syncthreads(); // publishes the next item; the tile / reduce scratch may be reused
+    }
+}
+
+struct BatchConfig {
+    int tile;
+    int ctas_per_sm; // 0 = as many as fit
+    const void *fn;
+    const char *name;
+};
+
+const std::vector<BatchConfig> &batch_configs()
+{
+    static const std::vector<BatchConfig> c = {
+        {64, 0, reinterpret_cast<const void *>(&batch_kernel<64>), "batch tile64 ctas/SM=max"},
+        {64, 4, reinterpret_cast<const void *>(&batch_kernel<64>), "batch tile64 ctas/SM=4"},
+        {32, 0, reinterpret_cast<const void *>(&batch_kernel<32>), "batch tile32 ctas/SM=max"},
+        {32, 8, reinterpret_cast<const void *>(&batch_kernel<32>), "batch tile32 ctas/SM=8"},
+    };
+    return c;
+}
+
+std::atomic<int> g_batch_choice{0};
+
+} // namespace
+
+int batch_num_configs() { return int(batch_configs().size()); }
+const char *batch_config_name(int c)
+{
+    return (c >= 0 && c < batch_num_configs()) ? batch_configs()[size_t(c)].name : nullptr;
+}
+int batch_selected() { return g_batch_choice.load(); }
+void batch_select(int c) { g_batch_choice.store(c); }
+
+int batch_tile(int config) { return batch_configs()[size_t(config)].tile; }
+
+namespace {
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+} // namespace
+
+BatchLayout batch_layout(int64_t count, int64_t items, int64_t chunks)
+{
+    BatchLayout L;
+    L.off_queue = 0;
+    L.off_done = 256;
+    L.off_inst = align_up(L.off_done + sizeof(unsigned) * size_t(std::max<int64_t>(count, 1)), 256);
+    L.off_items = align_up(L.off_inst + sizeof(BatchInst) * size_t(std::max<int64_t>(count, 1)), 256);
+    L.off_part = align_up(L.off_items + sizeof(uint32_t) * size_t(std::max<int64_t>(items, 1)), 256);
+    L.total = L.off_part + 8 * size_t(std::max<int64_t>(chunks, 1));
+    return L;
+}
+
+optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int tile, BatchTables &t)
+{
+    t.insts.assign(size_t(count), BatchInst{});
+    t.item_inst.clear();
+    t.items = t.chunks = t.bytes = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const optigpu_desc &d = descs[i];
+        BatchInst &b = t.insts[size_t(i)];
+        std::memset(&b, 0, sizeof b);
+        b.src = d.src;
+        b.dst = d.dst;
+        b.op = d.op;
+        b.dtype = d.dtype;
+        b.first_item = t.items;
+        const int64_t es = int64_t(esize_of(optigpu_dtype(d.dtype)));
+        int64_t n_items = 0;
+        if (d.op == OPTIGPU_OP_TRANSPOSE) {
+            b.rows = d.rows;
+            b.cols = d.cols;
+            if (d.rows > 0 && d.cols > 0) {
+                const int64_t tc = (d.cols + tile - 1) / tile;
+                const int64_t trn = (d.rows + tile - 1) / tile;
+                b.aux = tc;
+                n_items = tc * trn;
+                t.bytes += 2 * d.rows * d.cols * es;
+            }
+        } else {
+            b.rows = d.rows;
+            b.cols = 1;
+            b.vec_ok = (reinterpret_cast<uintptr_t>(d.src) & 15u) == 0 ? 1 : 0;
+            b.aux = t.chunks;
+            n_items = (d.rows + kReduceChunk - 1) / kReduceChunk;
+            t.chunks += n_items;
+            t.bytes += d.rows * es;
+        }
+        if (n_items > int64_t(0x7fffffff))
+            return fail(OPTIGPU_ERR_INVALID_ARG, "batch: instance too large");
+        b.nitems = int32_t(n_items);
+        t.item_inst.insert(t.item_inst.end(), size_t(n_items), uint32_t(i));
+        t.items += n_items;
+    }
+    return OPTIGPU_OK;
+}
+
+optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
+                            unsigned long long *d_queue, unsigned *d_done, void *d_partials, int compensated,
+                            cudaStream_t stream, int *grid_out)
+{
+    const BatchConfig &c = batch_configs()[size_t(config)];
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    int per_sm = 0;
+    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.fn, kBatchThreads, 0),
+                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)")) != OPTIGPU_OK)
+        return st;
+    per_sm = std::max(per_sm, 1);
+    if (c.ctas_per_sm > 0)
+        per_sm = std::min(per_sm, c.ctas_per_sm);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(per_sm) * dev.num_sms));
+    if ((st = check_cuda(cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), stream),
+                         "batch: reset queue")) != OPTIGPU_OK)
+        return st;
+    int comp = compensated;
+    void *args[] = {&d_insts, &d_item_inst, &items, &d_queue, &d_done, &d_partials, &comp};
+    if ((st = check_cuda(cudaLaunchKernel(c.fn, dim3(unsigned(grid)), dim3(kBatchThreads), args, 0, stream),
+                         "launch batch kernel")) != OPTIGPU_OK)
+        return st;
+    if (grid_out)
+        *grid_out = int(grid);
+    return OPTIGPU_OK;
+}
+
+optigpu_status batch_validate(const optigpu_desc &d, int32_t index);
+
+} // namespace optigpu
+
+// ------------------------------------------------------------------- plans
+
+struct optigpu_batch_plan {
+    int device = -1;
+    int config = 0;
+    uint32_t flags = 0;
+    int32_t count = 0;
+    int64_t total_items = 0;
+    int64_t total_chunks = 0;
+    int64_t bytes = 0;            // algorithmic bytes of one run
+    std::vector<optigpu_desc> descs;
+    // device workspace, one allocation
+    void *ws = nullptr;
+    optigpu::BatchInst *d_insts = nullptr;
+    uint32_t *d_item_inst = nullptr;
+    unsigned *d_inst_done = nullptr;
+    void *d_partials = nullptr;
+    unsigned long long *d_queue = nullptr;
+    // graph of one run
+    cudaGraphExec_t exec = nullptr;
+    int graph_config = -1;
+    int grid = 0;
+};
+
+namespace optigpu {
+namespace {
+
+std::mutex g_batch_mu;
+
+optigpu_status validate_desc_impl(const optigpu_desc &d, int32_t i)
+{
+    const std::string where = "batch descriptor " + std::to_string(i) + ": ";
+    if (d.op != OPTIGPU_OP_TRANSPOSE && d.op != OPTIGPU_OP_REDUCE)
+        return fail(OPTIGPU_ERR_INVALID_ARG, where + "unknown op");
+    if (!dtype_valid(d.dtype))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, where + "unknown dtype");
+    const size_t es = esize_of(optigpu_dtype(d.dtype));
+    if (d.op == OPTIGPU_OP_TRANSPOSE) {
+        if (d.rows < 0 || d.cols < 0)
+            return fail(OPTIGPU_ERR_INVALID_ARG, where + "negative rows or cols");
+        if (d.rows == 0 || d.cols == 0)
+            return OPTIGPU_OK;
+        if (d.rows > (int64_t(1) << 40) / d.cols)
+            return fail(OPTIGPU_ERR_INVALID_ARG, where + "rows * cols too large for one batch instance");
+        if (!d.src || !d.dst)
+            return fail(OPTIGPU_ERR_INVALID_ARG, where + "null pointer");
+        if ((reinterpret_cast<uintptr_t>(d.src) | reinterpret_cast<uintptr_t>(d.dst)) % es)
+            return fail(OPTIGPU_ERR_INVALID_ARG, where + "pointer not aligned to the element size");
+        const uintptr_t bytes = uintptr_t(d.rows * d.cols) * es;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(d.src), b = reinterpret_cast<uintptr_t>(d.dst);
+        if (a < b + bytes && b < a + bytes)
+            return fail(OPTIGPU_ERR_OVERLAP, where + "src and dst overlap");
+        return OPTIGPU_OK;
+    }
+    if (d.rows < 0 || d.rows > (int64_t(1) << 40))
+        return fail(OPTIGPU_ERR_INVALID_ARG, where + "n out of range");
+    if (!d.dst || reinterpret_cast<uintptr_t>(d.dst) % 8)
+        return fail(OPTIGPU_ERR_INVALID_ARG, where + "out must be a non-null 8-byte aligned pointer");
+    if (d.rows > 0 && (!d.src || reinterpret_cast<uintptr_t>(d.src) % es))
+        return fail(OPTIGPU_ERR_INVALID_ARG, where + "src must be non-null and element-aligned");
+    return OPTIGPU_OK;
+}
+
+void free_plan_device(optigpu_batch_plan *p)
+{
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->ws) {
+        cudaFree(p->ws);
+        p->ws = nullptr;
+    }
+}
+
+// Enqueues one run (queue reset + kernel) of `p` with configuration `config`
+// on `stream`.
+optigpu_status enqueue_run(optigpu_batch_plan *p, int config, cudaStream_t stream, int *grid_out)
+{
+    return batch_launch(config, p->d_insts, p->d_item_inst, p->total_items, p->d_queue, p->d_inst_done,
+                        p->d_partials, (p->flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, stream, grid_out);
+}
+
+// Builds the device tables of `p` for its current configuration (tile size).
+optigpu_status build_tables(optigpu_batch_plan *p)
+{
+    BatchTables t;
+    optigpu_status st = batch_tables(p->descs.data(), p->count, batch_tile(p->config), t);
+    if (st != OPTIGPU_OK)
+        return st;
+    p->total_items = t.items;
+    p->total_chunks = t.chunks;
+    p->bytes = t.bytes;
+    const BatchLayout L = batch_layout(p->count, t.items, t.chunks);
+    free_plan_device(p);
+    if ((st = check_cuda(cudaMalloc(&p->ws, L.total), "batch: cudaMalloc(workspace)")) != OPTIGPU_OK)
+        return st;
+    char *base = static_cast<char *>(p->ws);
+    p->d_queue = reinterpret_cast<unsigned long long *>(base + L.off_queue);
+    p->d_inst_done = reinterpret_cast<unsigned *>(base + L.off_done);
+    p->d_insts = reinterpret_cast<BatchInst *>(base + L.off_inst);
+    p->d_item_inst = reinterpret_cast<uint32_t *>(base + L.off_items);
+    p->d_partials = base + L.off_part;
+    if ((st = check_cuda(cudaMemset(p->ws, 0, L.off_inst), "batch: clear counters")) != OPTIGPU_OK)
+        return st;
+    if (p->count > 0 &&
+        (st = check_cuda(cudaMemcpy(p->d_insts, t.insts.data(), sizeof(BatchInst) * t.insts.size(),
+                                    cudaMemcpyHostToDevice),
+                         "batch: upload instances")) != OPTIGPU_OK)
+        return st;
+    if (t.items > 0 &&
+        (st = check_cuda(cudaMemcpy(p->d_item_inst, t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size(),
+                                    cudaMemcpyHostToDevice),
+                         "batch: upload item map")) != OPTIGPU_OK)
+        return st;
+    return OPTIGPU_OK;
+}
+
+} // namespace
+
+optigpu_status batch_validate(const optigpu_desc &d, int32_t index) { return validate_desc_impl(d, index); }
+
+namespace {
+
+// Captures one run into a CUDA graph on a private stream.
+optigpu_status build_graph(optigpu_batch_plan *p)
+{
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev); // caches device facts outside the capture
+    if (st != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "batch: cudaStreamCreate")) !=
+        OPTIGPU_OK)
+        return st;
+    cudaGraph_t graph = nullptr;
+    st = check_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
+    if (st == OPTIGPU_OK) {
+        const optigpu_status run = enqueue_run(p, p->config, cap, &p->grid);
+        st = check_cuda(cudaStreamEndCapture(cap, &graph), "batch: end capture");
+        if (run != OPTIGPU_OK)
+            st = run;
+    }
+    if (st == OPTIGPU_OK)
+        st = check_cuda(cudaGraphInstantiate(&p->exec, graph, 0), "batch: cudaGraphInstantiate");
+    if (graph)
+        cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (st == OPTIGPU_OK)
+        p->graph_config = p->config;
+    return st;
+}
+
+} // namespace
+} // namespace optigpu
+
+using namespace optigpu;
+
+extern "C" {
+
+optigpu_status optigpu_batch_plan_create(const optigpu_desc *descs, int32_t count, uint32_t flags,
+                                         optigpu_batch_plan **plan)
+{
+    if (!plan)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch: null plan pointer");
+    *plan = nullptr;
+    if (count < 0 || (count > 0 && !descs))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch: bad descriptor table");
+    if (flags & ~(OPTIGPU_REDUCE_COMPENSATED | OPTIGPU_BATCH_NO_GRAPH))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch: unknown flag bits");
+    for (int32_t i = 0; i < count; ++i) {
+        optigpu_status st = batch_validate(descs[i], i);
+        if (st != OPTIGPU_OK)
+            return st;
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    optigpu_batch_plan *p = new (std::nothrow) optigpu_batch_plan();
+    if (!p)
+        return fail(OPTIGPU_ERR_OOM, "batch: host allocation failed");
+    cudaGetDevice(&p->device);
+    p->flags = flags;
+    p->count = count;
+    p->descs.assign(descs, descs + count);
+    p->config = batch_selected();
+    optigpu_status st = build_tables(p);
+    if (st == OPTIGPU_OK && !(flags & OPTIGPU_BATCH_NO_GRAPH) && p->total_items > 0)
+        st = build_graph(p);
+    if (st != OPTIGPU_OK) {
+        free_plan_device(p);
+        delete p;
+        return st;
+    }
+    *plan = p;
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_batch_run(optigpu_batch_plan *plan, optigpu_stream_t stream)
+{
+    if (!plan)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch: null plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->total_items == 0) {
+        // Only empty instances: sums of nothing are 0.
+        for (const optigpu_desc &d : plan->descs)
+            if (d.op == OPTIGPU_OP_REDUCE) {
+                optigpu_status st = check_cuda(cudaMemsetAsync(d.dst, 0, 8, s), "batch: write 0");
+                if (st != OPTIGPU_OK)
+                    return st;
+            }
+        return OPTIGPU_OK;
+    }
+    // Sums of length 0 inside a batch have no chunk: write their zero first.
+    for (const optigpu_desc &d : plan->descs)
+        if (d.op == OPTIGPU_OP_REDUCE && d.rows == 0) {
+            optigpu_status st = check_cuda(cudaMemsetAsync(d.dst, 0, 8, s), "batch: write 0");
+            if (st != OPTIGPU_OK)
+                return st;
+        }
+    if (plan->exec && plan->graph_config == plan->config)
+        return check_cuda(cudaGraphLaunch(plan->exec, s), "batch: cudaGraphLaunch");
+    return enqueue_run(plan, plan->config, s, &plan->grid);
+}
+
+optigpu_status optigpu_batch_plan_info(const optigpu_batch_plan *plan, int64_t *items, int64_t *bytes,
+                                       int32_t *grid)
+{
+    if (!plan)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch: null plan");
+    if (items)
+        *items = plan->total_items;
+    if (bytes)
+        *bytes = plan->bytes;
+    if (grid)
+        *grid = plan->grid;
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_batch_autotune(optigpu_batch_plan *plan, int reps, optigpu_stream_t stream,
+                                      int *best_config, float *best_ms)
+{
+    if (!plan || reps < 1 || reps > 1000)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch_autotune: null plan or reps outside [1, 1000]");
+    if (plan->total_items == 0)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "batch_autotune: empty plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    optigpu_status st = check_cuda(cudaEventCreate(&a), "cudaEventCreate");
+    if (st == OPTIGPU_OK)
+        st = check_cuda(cudaEventCreate(&b), "cudaEventCreate");
+    int best = -1;
+    float best_t = 0.f;
+    for (int c = 0; st == OPTIGPU_OK && c < batch_num_configs(); ++c) {
+        plan->config = c;
+        if ((st = build_tables(plan)) != OPTIGPU_OK)
+            break;
+        std::vector<float> t;
+        for (int r = 0; r < reps + 1 && st == OPTIGPU_OK; ++r) {
+            cudaEventRecord(a, s);
+            st = enqueue_run(plan, c, s, &plan->grid);
+            cudaEventRecord(b, s);
+            if (st == OPTIGPU_OK)
+                st = check_cuda(cudaEventSynchronize(b), "cudaEventSynchronize");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (r > 0)
+                t.push_back(ms);
+        }
+        if (st != OPTIGPU_OK)
+            break;
+        std::sort(t.begin(), t.end());
+        if (best < 0 || t[t.size() / 2] < best_t) {
+            best = c;
+            best_t = t[t.size() / 2];
+        }
+    }
+    if (a)
+        cudaEventDestroy(a);
+    if (b)
+        cudaEventDestroy(b);
+    if (st != OPTIGPU_OK)
+        return st;
+    plan->config = best;
+    batch_select(best);
+    if ((st = build_tables(plan)) != OPTIGPU_OK)
+        return st;
+    if (!(plan->flags & OPTIGPU_BATCH_NO_GRAPH) && (st = build_graph(plan)) != OPTIGPU_OK)
+        return st;
+    if (best_config)
+        *best_config = best;
+    if (best_ms)
+        *best_ms = best_t;
+    return OPTIGPU_OK;
+}
+
+void optigpu_batch_plan_destroy(optigpu_batch_plan *plan)
+{
+    if (!plan)
+        return;
+    free_plan_device(plan);
+    delete plan;
+}
+
+} // extern "C"

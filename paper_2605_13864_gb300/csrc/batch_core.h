@@ -1,0 +1,61 @@
+// batch_core.h -- the batch kernel's device tables and the helpers that
+// build and launch them, shared by batch plans (batch.cu) and the serving
+// engine (server.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/optigpu.h"
+
+namespace optigpu {
+
+// Device-side description of one instance.
+struct BatchInst {
+    const void *src;
+    void *dst;
+    int64_t rows;       // transpose rows, or the sum length n
+    int64_t cols;       // transpose cols (1 for sums)
+    int64_t first_item; // index of this instance's first work item
+    int64_t aux;        // transpose: tiles per tile-row; sum: offset of its partials
+    int32_t op;         // OPTIGPU_OP_TRANSPOSE / OPTIGPU_OP_REDUCE
+    int32_t dtype;
+    int32_t nitems;     // tiles or chunks
+    int32_t vec_ok;     // sum: 16-byte aligned source
+};
+
+// Host image of one batch: instances, the item -> instance map and totals.
+struct BatchTables {
+    std::vector<BatchInst> insts;
+    std::vector<uint32_t> item_inst;
+    int64_t items = 0;  // work items
+    int64_t chunks = 0; // sum chunks (partial slots)
+    int64_t bytes = 0;  // algorithmic bytes
+};
+
+// Byte offsets of one batch workspace: [queue][done counters][instances]
+// [item map][partials].
+struct BatchLayout {
+    size_t off_queue, off_done, off_inst, off_items, off_part, total;
+};
+
+BatchLayout batch_layout(int64_t count, int64_t items, int64_t chunks);
+
+// Checks one descriptor like the single calls do.
+optigpu_status batch_validate(const optigpu_desc &d, int32_t index);
+
+// Fills `t` for `count` validated descriptors, transposes cut in tile x tile.
+optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int tile, BatchTables &t);
+
+// Transpose tile of batch configuration `config`.
+int batch_tile(int config);
+
+// Enqueues the queue reset and the persistent batch kernel on `stream`.
+optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
+                            unsigned long long *d_queue, unsigned *d_done, void *d_partials, int compensated,
+                            cudaStream_t stream, int *grid_out);
+
+} // namespace optigpu

@@ -77,4 +77,10 @@ void reduce_select(int config);
 optigpu_status reduce_dispatch(const void *src, int64_t n, int dtype, void *out, uint32_t flags,
                                cudaStream_t stream);
 
+// Batch kernel configurations (default of new plans).
+int batch_num_configs();
+const char *batch_config_name(int config);
+int batch_selected();
+void batch_select(int config);
+
 } // namespace optigpu

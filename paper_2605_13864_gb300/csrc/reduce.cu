@@ -190,6 +190,15 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n, optigpu_dtype d
     return reduce_dispatch(src, n, int(dtype), out, flags, static_cast<cudaStream_t>(stream));
 }
 
+optigpu_status optigpu_reduce_reserve(int64_t n, optigpu_stream_t stream)
+{
+    if (n < 0 || n > (int64_t(1) << 62))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_reserve: n out of range");
+    const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
+    void *ws = nullptr;
+    return stream_workspace(static_cast<cudaStream_t>(stream), kReduceCounterBytes + size_t(num_chunks) * 8, &ws);
+}
+
 } // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,556 @@
+// server.cu -- continuous-batching request server for transposes and sums.
+//
+// Requests carry host buffers.  submit() queues a request; step() does one
+// round of the serving loop:
+//   1. completion: every stream whose completion event has fired releases its
+//      requests -- their device buffers go back to the arena, their slots are
+//      freed, and they are marked done (results are in their host buffers);
+//   2. admission: while a stream is free, queued requests are admitted in
+//      arrival order as long as a slot is free and their input + output fit
+//      in the device-memory budget (an arena carved out of one allocation);
+//   3. launch: the admitted requests' inputs are copied in, the step's batch
+//      runs as ONE persistent batch kernel built from per-step tables (the
+//      kernel of batch.cu: same chunks, same results as the single calls),
+//      the outputs are copied back, and an event marks the step's end.
+// Requests that arrive while earlier steps run are admitted into the next
+// step on another stream, so their copies and kernels overlap on the device.
+//
+// With OPTIGPU_SERVER_PER_CALL the same loop launches one plain kernel per
+// request (optigpu_transpose / optigpu_reduce_sum_ex), one request per
+// stream: the per-call baseline.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch_core.h"
+#include "internal.h"
+#include "reduce_core.cuh"
+
+namespace optigpu {
+
+optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
+                                  cudaStream_t stream);
+
+namespace {
+
+double now_s()
+{
+    using clk = std::chrono::steady_clock;
+    return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+constexpr size_t kAlign = 256;
+size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Best-fit allocator over one device allocation; free ranges coalesce.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0, peak = 0;
+    std::map<size_t, size_t> free_ranges; // offset -> length
+
+    void reset(char *b, size_t n)
+    {
+        base = b;
+        size = n;
+        used = peak = 0;
+        free_ranges.clear();
+        if (n)
+            free_ranges[0] = n;
+    }
+
+    bool alloc(size_t bytes, size_t &off)
+    {
+        bytes = round_up(std::max<size_t>(bytes, 1));
+        auto best = free_ranges.end();
+        for (auto it = free_ranges.begin(); it != free_ranges.end(); ++it)
+            if (it->second >= bytes && (best == free_ranges.end() || it->second < best->second))
+                best = it;
+        if (best == free_ranges.end())
+            return false;
+        off = best->first;
+        const size_t len = best->second;
+        free_ranges.erase(best);
+        if (len > bytes)
+            free_ranges[off + bytes] = len - bytes;
+        used += bytes;
+        peak = std::max(peak, used);
+        return true;
+    }
+
+    void release(size_t off, size_t bytes)
+    {
+        bytes = round_up(std::max<size_t>(bytes, 1));
+        used -= bytes;
+        auto next = free_ranges.lower_bound(off);
+        size_t start = off, len = bytes;
+        if (next != free_ranges.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                start = prev->first;
+                len += prev->second;
+                free_ranges.erase(prev);
+            }
+        }
+        next = free_ranges.lower_bound(off + bytes);
+        if (next != free_ranges.end() && next->first == off + bytes) {
+            len += next->second;
+            free_ranges.erase(next);
+        }
+        free_ranges[start] = len;
+    }
+};
+
+enum ReqState { QUEUED = 0, RUNNING = 1, DONE = 2 };
+
+struct Req {
+    optigpu_request r{};
+    size_t in_bytes = 0, out_bytes = 0;
+    size_t off_in = 0, off_out = 0;
+    int state = QUEUED;
+    double t_submit = 0, t_done = 0;
+    int64_t trace_index = -1;
+};
+
+struct StreamCtx {
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+    // per-step batch tables: device workspace and pinned host staging
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    void *h_stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+} // namespace
+} // namespace optigpu
+
+struct optigpu_server {
+    std::mutex mu;
+    size_t budget = 0;
+    int32_t max_slots = 0;
+    uint32_t flags = 0;
+    int device = -1;
+    void *arena_mem = nullptr;
+    optigpu::Arena arena;
+    std::vector<optigpu::StreamCtx> streams;
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, optigpu::Req> reqs;
+    uint64_t next_ticket = 1;
+    int32_t running = 0;
+    optigpu_server_stats stats{};
+    std::vector<double> *trace_done = nullptr; // completion times by trace index (replay)
+};
+
+namespace optigpu {
+namespace {
+
+optigpu_status validate_request(const optigpu_server *sv, const optigpu_request &r, size_t &in_b, size_t &out_b)
+{
+    if (r.op != OPTIGPU_OP_TRANSPOSE && r.op != OPTIGPU_OP_REDUCE)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: unknown op");
+    if (!dtype_valid(r.dtype))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "server: unknown dtype");
+    const size_t es = esize_of(optigpu_dtype(r.dtype));
+    const int64_t cols = r.op == OPTIGPU_OP_TRANSPOSE ? r.cols : 1;
+    if (r.rows < 0 || cols < 0 || (cols > 0 && r.rows > (int64_t(1) << 40) / cols))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: bad size");
+    const size_t n = size_t(r.rows) * size_t(cols);
+    in_b = n * es;
+    out_b = r.op == OPTIGPU_OP_TRANSPOSE ? n * es : 8;
+    if ((in_b && !r.host_src) || (out_b && !r.host_dst))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null host buffer");
+    if (round_up(std::max<size_t>(in_b, 1)) + round_up(out_b) > sv->budget)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: request larger than the memory budget");
+    return OPTIGPU_OK;
+}
+
+// Releases the requests of every stream whose step has finished.
+optigpu_status complete_finished(optigpu_server *sv)
+{
+    for (StreamCtx &sc : sv->streams) {
+        if (!sc.busy)
+            continue;
+        const cudaError_t q = cudaEventQuery(sc.done);
+        if (q == cudaErrorNotReady)
+            continue;
+        if (q != cudaSuccess)
+            return check_cuda(q, "server: step failed");
+        const double t = now_s();
+        for (uint64_t tk : sc.tickets) {
+            Req &rq = sv->reqs[tk];
+            sv->arena.release(rq.off_in, rq.in_bytes);
+            sv->arena.release(rq.off_out, rq.out_bytes);
+            rq.state = DONE;
+            rq.t_done = t;
+            if (sv->trace_done && rq.trace_index >= 0)
+                (*sv->trace_done)[size_t(rq.trace_index)] = t;
+            --sv->running;
+            ++sv->stats.completed;
+        }
+        sc.tickets.clear();
+        sc.busy = false;
+    }
+    return OPTIGPU_OK;
+}
+
+optigpu_status ensure_capacity(StreamCtx &sc, size_t ws_bytes, size_t stage_bytes)
+{
+    optigpu_status st;
+    if (sc.ws_bytes < ws_bytes) {
+        if (sc.d_ws)
+            cudaFree(sc.d_ws);
+        sc.d_ws = nullptr;
+        sc.ws_bytes = 0;
+        const size_t want = std::max<size_t>(ws_bytes * 2, size_t(1) << 20);
+        if ((st = check_cuda(cudaMalloc(&sc.d_ws, want), "server: cudaMalloc(step workspace)")) != OPTIGPU_OK)
+            return st;
+        if ((st = check_cuda(cudaMemset(sc.d_ws, 0, want), "server: clear step workspace")) != OPTIGPU_OK)
+            return st;
+        sc.ws_bytes = want;
+    }
+    if (sc.stage_bytes < stage_bytes) {
+        if (sc.h_stage)
+            cudaFreeHost(sc.h_stage);
+        sc.h_stage = nullptr;
+        sc.stage_bytes = 0;
+        const size_t want = std::max<size_t>(stage_bytes * 2, size_t(1) << 20);
+        if ((st = check_cuda(cudaMallocHost(&sc.h_stage, want), "server: cudaMallocHost(stage)")) != OPTIGPU_OK)
+            return st;
+        sc.stage_bytes = want;
+    }
+    return OPTIGPU_OK;
+}
+
+// Launches the admitted tickets `adm` on `sc`.
+optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<uint64_t> &adm)
+{
+    optigpu_status st = OPTIGPU_OK;
+    char *base = sv->arena.base;
+    for (uint64_t tk : adm) {
+        const Req &rq = sv->reqs[tk];
+        if (rq.in_bytes &&
+            (st = check_cuda(cudaMemcpyAsync(base + rq.off_in, rq.r.host_src, rq.in_bytes, cudaMemcpyHostToDevice, sc.s),
+                             "server: copy in")) != OPTIGPU_OK)
+            return st;
+    }
+    const bool per_call = (sv->flags & OPTIGPU_SERVER_PER_CALL) != 0;
+    const uint32_t rflags = sv->flags & OPTIGPU_REDUCE_COMPENSATED;
+    if (per_call) {
+        for (uint64_t tk : adm) {
+            const Req &rq = sv->reqs[tk];
+            if (rq.r.op == OPTIGPU_OP_TRANSPOSE)
+                st = transpose_dispatch(base + rq.off_in, base + rq.off_out, rq.r.rows, rq.r.cols, rq.r.dtype,
+                                        OPTIGPU_TRANSPOSE_AUTO, sc.s);
+            else
+                st = reduce_dispatch(base + rq.off_in, rq.r.rows, rq.r.dtype, base + rq.off_out, rflags, sc.s);
+            if (st != OPTIGPU_OK)
+                return st;
+            ++sv->stats.launches;
+        }
+    } else {
+        std::vector<optigpu_desc> descs;
+        descs.reserve(adm.size());
+        for (uint64_t tk : adm) {
+            const Req &rq = sv->reqs[tk];
+            optigpu_desc d{};
+            d.op = rq.r.op;
+            d.dtype = rq.r.dtype;
+            d.src = base + rq.off_in;
+            d.dst = base + rq.off_out;
+            d.rows = rq.r.rows;
+            d.cols = rq.r.op == OPTIGPU_OP_TRANSPOSE ? rq.r.cols : 1;
+            descs.push_back(d);
+            if (d.op == OPTIGPU_OP_REDUCE && d.rows == 0 &&
+                (st = check_cuda(cudaMemsetAsync(d.dst, 0, 8, sc.s), "server: zero sum")) != OPTIGPU_OK)
+                return st;
+        }
+        const int config = batch_selected();
+        BatchTables t;
+        if ((st = batch_tables(descs.data(), int32_t(descs.size()), batch_tile(config), t)) != OPTIGPU_OK)
+            return st;
+        if (t.items > 0) {
+            const BatchLayout L = batch_layout(int64_t(descs.size()), t.items, t.chunks);
+            const size_t table_bytes = L.off_part - L.off_inst;
+            if ((st = ensure_capacity(sc, L.total, table_bytes)) != OPTIGPU_OK)
+                return st;
+            char *stage = static_cast<char *>(sc.h_stage);
+            std::memcpy(stage, t.insts.data(), sizeof(BatchInst) * t.insts.size());
+            std::memcpy(stage + (L.off_items - L.off_inst), t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size());
+            char *ws = static_cast<char *>(sc.d_ws);
+            if ((st = check_cuda(cudaMemcpyAsync(ws + L.off_inst, stage, table_bytes, cudaMemcpyHostToDevice, sc.s),
+                                 "server: copy step tables")) != OPTIGPU_OK)
+                return st;
+            if ((st = batch_launch(config, reinterpret_cast<BatchInst *>(ws + L.off_inst),
+                                   reinterpret_cast<uint32_t *>(ws + L.off_items), t.items,
+                                   reinterpret_cast<unsigned long long *>(ws + L.off_queue),
+                                   reinterpret_cast<unsigned *>(ws + L.off_done), ws + L.off_part,
+                                   rflags ? 1 : 0, sc.s, nullptr)) != OPTIGPU_OK)
+                return st;
+            ++sv->stats.launches;
+        }
+    }
+    for (uint64_t tk : adm) {
+        const Req &rq = sv->reqs[tk];
+        if (rq.out_bytes &&
+            (st = check_cuda(cudaMemcpyAsync(rq.r.host_dst, base + rq.off_out, rq.out_bytes, cudaMemcpyDeviceToHost,
+                                             sc.s),
+                             "server: copy out")) != OPTIGPU_OK)
+            return st;
+    }
+    if ((st = check_cuda(cudaEventRecord(sc.done, sc.s), "server: record step event")) != OPTIGPU_OK)
+        return st;
+    sc.busy = true;
+    sc.tickets = adm;
+    ++sv->stats.steps;
+    return OPTIGPU_OK;
+}
+
+optigpu_status step_locked(optigpu_server *sv, int32_t *launched)
+{
+    if (launched)
+        *launched = 0;
+    optigpu_status st = complete_finished(sv);
+    if (st != OPTIGPU_OK)
+        return st;
+    const bool per_call = (sv->flags & OPTIGPU_SERVER_PER_CALL) != 0;
+    for (StreamCtx &sc : sv->streams) {
+        if (sc.busy)
+            continue;
+        if (sv->pending.empty())
+            break;
+        std::vector<uint64_t> adm;
+        while (!sv->pending.empty() && sv->running < sv->max_slots) {
+            Req &rq = sv->reqs[sv->pending.front()];
+            size_t a = 0, b = 0;
+            if (!sv->arena.alloc(rq.in_bytes, a))
+                break;
+            if (!sv->arena.alloc(rq.out_bytes, b)) {
+                sv->arena.release(a, rq.in_bytes);
+                break;
+            }
+            rq.off_in = a;
+            rq.off_out = b;
+            rq.state = RUNNING;
+            ++sv->running;
+            adm.push_back(sv->pending.front());
+            sv->pending.pop_front();
+            if (per_call)
+                break; // one request per stream
+        }
+        if (adm.empty())
+            break; // out of slots or budget: wait for completions
+        if ((st = launch_step(sv, sc, adm)) != OPTIGPU_OK)
+            return st;
+        if (launched)
+            ++*launched;
+    }
+    sv->stats.pending = int64_t(sv->pending.size());
+    sv->stats.in_flight = sv->running;
+    sv->stats.max_in_flight = std::max<int64_t>(sv->stats.max_in_flight, sv->running);
+    sv->stats.bytes_in_use = int64_t(sv->arena.used);
+    sv->stats.peak_bytes = int64_t(sv->arena.peak);
+    return OPTIGPU_OK;
+}
+
+optigpu_status submit_locked(optigpu_server *sv, const optigpu_request &r, int64_t trace_index, uint64_t *ticket)
+{
+    size_t in_b = 0, out_b = 0;
+    optigpu_status st = validate_request(sv, r, in_b, out_b);
+    if (st != OPTIGPU_OK)
+        return st;
+    const uint64_t tk = sv->next_ticket++;
+    Req rq;
+    rq.r = r;
+    rq.in_bytes = in_b;
+    rq.out_bytes = out_b;
+    rq.t_submit = now_s();
+    rq.trace_index = trace_index;
+    sv->reqs.emplace(tk, rq);
+    sv->pending.push_back(tk);
+    ++sv->stats.submitted;
+    if (ticket)
+        *ticket = tk;
+    return OPTIGPU_OK;
+}
+
+void destroy_server(optigpu_server *sv)
+{
+    for (StreamCtx &sc : sv->streams) {
+        if (sc.s)
+            cudaStreamSynchronize(sc.s);
+        if (sc.done)
+            cudaEventDestroy(sc.done);
+        if (sc.d_ws)
+            cudaFree(sc.d_ws);
+        if (sc.h_stage)
+            cudaFreeHost(sc.h_stage);
+        if (sc.s)
+            cudaStreamDestroy(sc.s);
+    }
+    if (sv->arena_mem)
+        cudaFree(sv->arena_mem);
+    delete sv;
+}
+
+} // namespace
+} // namespace optigpu
+
+using namespace optigpu;
+
+extern "C" {
+
+optigpu_status optigpu_server_create(size_t mem_budget_bytes, int32_t max_slots, int32_t n_streams, uint32_t flags,
+                                     optigpu_server **out)
+{
+    if (!out)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null output pointer");
+    *out = nullptr;
+    if (mem_budget_bytes < (size_t(1) << 20) || max_slots < 1 || n_streams < 1 || n_streams > 1024)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: budget >= 1 MiB, max_slots >= 1, n_streams in [1, 1024]");
+    if (flags & ~(OPTIGPU_REDUCE_COMPENSATED | OPTIGPU_SERVER_PER_CALL))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: unknown flag bits");
+    optigpu_server *sv = new (std::nothrow) optigpu_server();
+    if (!sv)
+        return fail(OPTIGPU_ERR_OOM, "server: host allocation failed");
+    sv->budget = mem_budget_bytes;
+    sv->max_slots = max_slots;
+    sv->flags = flags;
+    cudaGetDevice(&sv->device);
+    optigpu_status st = check_cuda(cudaMalloc(&sv->arena_mem, mem_budget_bytes), "server: cudaMalloc(budget)");
+    if (st == OPTIGPU_OK) {
+        sv->arena.reset(static_cast<char *>(sv->arena_mem), mem_budget_bytes);
+        sv->streams.resize(size_t(n_streams));
+        for (StreamCtx &sc : sv->streams) {
+            if ((st = check_cuda(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking), "server: stream")) != OPTIGPU_OK)
+                break;
+            if ((st = check_cuda(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming), "server: event")) !=
+                OPTIGPU_OK)
+                break;
+        }
+    }
+    if (st != OPTIGPU_OK) {
+        destroy_server(sv);
+        return st;
+    }
+    *out = sv;
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_server_submit(optigpu_server *sv, const optigpu_request *req, uint64_t *ticket)
+{
+    if (!sv || !req)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null server or request");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->max_slots > 0 && int64_t(sv->pending.size()) >= int64_t(1) << 24)
+        return fail(OPTIGPU_ERR_BUSY, "server: queue full");
+    return submit_locked(sv, *req, -1, ticket);
+}
+
+optigpu_status optigpu_server_step(optigpu_server *sv, int32_t *launched)
+{
+    if (!sv)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    return step_locked(sv, launched);
+}
+
+optigpu_status optigpu_server_poll(optigpu_server *sv, uint64_t ticket, int32_t *done)
+{
+    if (!sv || !done)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    optigpu_status st = complete_finished(sv);
+    if (st != OPTIGPU_OK)
+        return st;
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end())
+        return fail(OPTIGPU_ERR_NOT_FOUND, "server: unknown ticket");
+    *done = it->second.state == DONE ? 1 : 0;
+    if (*done)
+        sv->reqs.erase(it);
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_server_drain(optigpu_server *sv)
+{
+    if (!sv)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null server");
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            optigpu_status st = step_locked(sv, nullptr);
+            if (st != OPTIGPU_OK)
+                return st;
+            if (sv->pending.empty() && sv->running == 0)
+                return OPTIGPU_OK;
+        }
+        std::this_thread::yield();
+    }
+}
+
+optigpu_status optigpu_server_get_stats(optigpu_server *sv, optigpu_server_stats *out)
+{
+    if (!sv || !out)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->pending = int64_t(sv->pending.size());
+    out->in_flight = sv->running;
+    out->bytes_in_use = int64_t(sv->arena.used);
+    out->peak_bytes = int64_t(sv->arena.peak);
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_server_replay(optigpu_server *sv, const optigpu_request *reqs, const double *arrival_s,
+                                     int64_t count, double *latency_s)
+{
+    if (!sv || count < 0 || (count > 0 && (!reqs || !arrival_s || !latency_s)))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server_replay: bad arguments");
+    for (int64_t i = 1; i < count; ++i)
+        if (arrival_s[i] < arrival_s[i - 1])
+            return fail(OPTIGPU_ERR_INVALID_ARG, "server_replay: arrival times must be non-decreasing");
+    std::vector<double> done(size_t(count), -1.0);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->trace_done = &done;
+    const int64_t completed0 = sv->stats.completed;
+    const double t0 = now_s();
+    int64_t next = 0;
+    optigpu_status st = OPTIGPU_OK;
+    while (sv->stats.completed - completed0 < count) {
+        const double t = now_s() - t0;
+        while (next < count && arrival_s[next] <= t) {
+            if ((st = submit_locked(sv, reqs[next], next, nullptr)) != OPTIGPU_OK)
+                break;
+            ++next;
+        }
+        if (st != OPTIGPU_OK || (st = step_locked(sv, nullptr)) != OPTIGPU_OK)
+            break;
+    }
+    sv->trace_done = nullptr;
+    // Replayed tickets are not polled: forget every finished one.
+    for (auto it = sv->reqs.begin(); it != sv->reqs.end();)
+        it = (it->second.state == DONE && it->second.trace_index >= 0) ? sv->reqs.erase(it) : std::next(it);
+    if (st != OPTIGPU_OK)
+        return st;
+    for (int64_t i = 0; i < count; ++i)
+        latency_s[i] = done[size_t(i)] - (t0 + arrival_s[i]);
+    return OPTIGPU_OK;
+}
+
+void optigpu_server_destroy(optigpu_server *sv)
+{
+    if (sv)
+        destroy_server(sv);
+}
+
+} // extern "C"

@@ -26,7 +26,10 @@ namespace {
 
 std::mutex g_tune_mu;
 
-bool op_dtype_ok(int op, int dtype) { return (op == OPTIGPU_OP_TRANSPOSE || op == OPTIGPU_OP_REDUCE) && dtype_valid(dtype); }
+bool op_dtype_ok(int op, int dtype)
+{
+    return op == OPTIGPU_OP_BATCH || ((op == OPTIGPU_OP_TRANSPOSE || op == OPTIGPU_OP_REDUCE) && dtype_valid(dtype));
+}
 
 struct Events {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -100,6 +103,8 @@ int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype)
 {
     if (!op_dtype_ok(op, dtype))
         return -1;
+    if (op == OPTIGPU_OP_BATCH)
+        return batch_num_configs();
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_num_configs(esize_of(dtype)) : reduce_num_configs();
 }
 
@@ -107,6 +112,8 @@ const char *optigpu_tune_config_name(optigpu_op op, optigpu_dtype dtype, int con
 {
     if (!op_dtype_ok(op, dtype))
         return nullptr;
+    if (op == OPTIGPU_OP_BATCH)
+        return batch_config_name(config);
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_config_name(esize_of(dtype), config) : reduce_config_name(config);
 }
 
@@ -116,7 +123,9 @@ optigpu_status optigpu_tune_select(optigpu_op op, optigpu_dtype dtype, int confi
         return fail(OPTIGPU_ERR_INVALID_ARG, "tune: unknown op or dtype");
     if (config < 0 || config >= optigpu_tune_num_configs(op, dtype))
         return fail(OPTIGPU_ERR_INVALID_ARG, "tune: configuration index out of range");
-    if (op == OPTIGPU_OP_TRANSPOSE)
+    if (op == OPTIGPU_OP_BATCH)
+        batch_select(config);
+    else if (op == OPTIGPU_OP_TRANSPOSE)
         transpose_select(esize_of(dtype), config);
     else
         reduce_select(config);
@@ -127,6 +136,8 @@ int optigpu_tune_selected(optigpu_op op, optigpu_dtype dtype)
 {
     if (!op_dtype_ok(op, dtype))
         return -1;
+    if (op == OPTIGPU_OP_BATCH)
+        return batch_selected();
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_selected(esize_of(dtype)) : reduce_selected();
 }
 
@@ -153,8 +164,8 @@ int64_t optigpu_tune_get_param(const char *name)
 optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows, int64_t cols, int reps,
                                 optigpu_stream_t stream, int *best_config, float *best_ms)
 {
-    if (!op_dtype_ok(op, dtype))
-        return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: unknown op or dtype");
+    if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: unknown op or dtype (batches: optigpu_batch_autotune)");
     if (rows <= 0 || cols <= 0 || rows > (int64_t(1) << 31) || cols > (int64_t(1) << 31) || reps < 1 ||
         reps > 1000)
         return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: rows, cols in [1, 2^31], reps in [1, 1000]");
@@ -223,6 +234,7 @@ optigpu_status optigpu_tune_save(const char *path)
         (void)dt;
     }
     f << "reduce " << reduce_config_name(reduce_selected()) << "\n";
+    f << "batch " << batch_config_name(batch_selected()) << "\n";
     f << "param transpose.group_rows " << transpose_group_rows() << "\n";
     return f ? OPTIGPU_OK : fail(OPTIGPU_ERR_INVALID_ARG, "tune_save: write failed");
 }
@@ -258,6 +270,14 @@ optigpu_status optigpu_tune_load(const char *path)
             for (int c = 0; c < reduce_num_configs(); ++c)
                 if (name == reduce_config_name(c)) {
                     reduce_select(c);
+                    ++applied;
+                }
+        } else if (kind == "batch") {
+            std::string name;
+            std::getline(in >> std::ws, name);
+            for (int c = 0; c < batch_num_configs(); ++c)
+                if (name == batch_config_name(c)) {
+                    batch_select(c);
                     ++applied;
                 }
         } else if (kind == "param") {

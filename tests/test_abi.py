@@ -115,3 +115,80 @@ def test_reduce_validation(lib, args, status):
 def test_errors_carry_a_message(lib):
     lib.optigpu_reduce_sum_ex(FAKE, 10, 17, FAKE, 0, None)
     assert b"dtype" in lib.optigpu_last_error()
+
+
+def _desc_array(rows):
+    arr = (N.Desc * len(rows))()
+    for k, (op, dt, src, dst, r, c) in enumerate(rows):
+        arr[k].op, arr[k].dtype, arr[k].src, arr[k].dst, arr[k].rows, arr[k].cols = op, dt, src, dst, r, c
+    return arr
+
+
+@pytest.mark.parametrize("rows,status", [
+    ([(5, N.FLOAT32, FAKE, FAKE + (1 << 20), 4, 4)], N.ERR_INVALID_ARG),            # unknown op
+    ([(N.OP_TRANSPOSE, 9, FAKE, FAKE + (1 << 20), 4, 4)], N.ERR_UNSUPPORTED_DTYPE),
+    ([(N.OP_TRANSPOSE, N.FLOAT32, FAKE, FAKE + 8, 4, 4)], N.ERR_OVERLAP),
+    ([(N.OP_TRANSPOSE, N.FLOAT32, None, FAKE, 4, 4)], N.ERR_INVALID_ARG),
+    ([(N.OP_REDUCE, N.FLOAT32, FAKE, FAKE + 4, 10, 1)], N.ERR_INVALID_ARG),          # out not 8-aligned
+    ([(N.OP_REDUCE, N.FLOAT32, FAKE, FAKE + 64, -1, 1)], N.ERR_INVALID_ARG),
+    ([(N.OP_TRANSPOSE, N.FLOAT32, FAKE, FAKE + (1 << 30), 4, 4),
+      (N.OP_REDUCE, N.BFLOAT16, FAKE + 1, FAKE + 64, 10, 1)], N.ERR_INVALID_ARG),  # 2nd bad
+])
+def test_batch_plan_validation(lib, rows, status):
+    plan = ctypes.c_void_p()
+    arr = _desc_array(rows)
+    assert lib.optigpu_batch_plan_create(arr, len(rows), 0, ctypes.byref(plan)) == status
+    assert not plan.value
+
+
+def test_batch_plan_rejects_bad_flags_and_tables(lib):
+    plan = ctypes.c_void_p()
+    assert lib.optigpu_batch_plan_create(None, 3, 0, ctypes.byref(plan)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_batch_plan_create(None, -1, 0, ctypes.byref(plan)) == N.ERR_INVALID_ARG
+    arr = _desc_array([(N.OP_REDUCE, N.FLOAT32, FAKE, FAKE + 64, 10, 1)])
+    assert lib.optigpu_batch_plan_create(arr, 1, 1 << 7, ctypes.byref(plan)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_batch_run(None, None) == N.ERR_INVALID_ARG
+
+
+def test_tune_tables_are_host_only(lib):
+    for op, dt in ((N.OP_TRANSPOSE, N.FLOAT32), (N.OP_TRANSPOSE, N.BFLOAT16), (N.OP_REDUCE, N.FLOAT32),
+                   (N.OP_BATCH, 0)):
+        n = lib.optigpu_tune_num_configs(op, dt)
+        assert n >= 2
+        names = [lib.optigpu_tune_config_name(op, dt, i) for i in range(n)]
+        assert all(names) and len(set(names)) == n
+        assert lib.optigpu_tune_config_name(op, dt, n) is None
+    assert lib.optigpu_tune_select(N.OP_REDUCE, N.FLOAT32, 99) == N.ERR_INVALID_ARG
+    assert lib.optigpu_tune_set_param(b"no.such.param", 1) == N.ERR_NOT_FOUND
+    assert lib.optigpu_tune_set_param(b"transpose.group_rows", 0) == N.ERR_INVALID_ARG
+    assert lib.optigpu_tune_get_param(b"transpose.group_rows") >= 1
+
+
+def test_tune_cache_round_trip(lib, tmp_path):
+    path = str(tmp_path / "tune.txt").encode()
+    assert lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 1) == N.OK
+    assert lib.optigpu_tune_set_param(b"transpose.group_rows", 8) == N.OK
+    assert lib.optigpu_tune_save(path) == N.OK
+    assert lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 0) == N.OK
+    assert lib.optigpu_tune_set_param(b"transpose.group_rows", 16) == N.OK
+    assert lib.optigpu_tune_load(path) == N.OK
+    assert lib.optigpu_tune_selected(N.OP_TRANSPOSE, N.FLOAT32) == 1
+    assert lib.optigpu_tune_get_param(b"transpose.group_rows") == 8
+    assert lib.optigpu_tune_load(b"/nonexistent/tune.txt") == N.ERR_NOT_FOUND
+    lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 0)
+    lib.optigpu_tune_set_param(b"transpose.group_rows", 16)
+
+
+def test_server_validation_is_host_side(lib):
+    sv = ctypes.c_void_p()
+    assert lib.optigpu_server_create(1 << 10, 4, 2, 0, ctypes.byref(sv)) == N.ERR_INVALID_ARG   # budget < 1 MiB
+    assert lib.optigpu_server_create(1 << 30, 0, 2, 0, ctypes.byref(sv)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_create(1 << 30, 4, 0, 0, ctypes.byref(sv)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_create(1 << 30, 4, 2, 1 << 9, ctypes.byref(sv)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_create(1 << 30, 4, 2, 0, None) == N.ERR_INVALID_ARG
+    assert not sv.value
+    assert lib.optigpu_server_submit(None, None, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_step(None, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_drain(None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_server_replay(None, None, None, 1, None) == N.ERR_INVALID_ARG
+    lib.optigpu_server_destroy(None)
