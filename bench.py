@@ -490,6 +490,50 @@ def run_gpu(args):
     return 0
 
 
+def run_case(args):
+    """Runs one named kernel case `args.case_reps` times on a small problem
+    and exits: the target of ncu captures (no timing, no JSON)."""
+    import torch
+    from paper_2605_13864_gb300 import api, workloads
+
+    torch.cuda.set_device(0)
+    side, case = args.side, args.case
+    if case.startswith("transpose"):
+        dt = torch.bfloat16 if case.endswith("bf16") else torch.float32
+        kernel = "tile32" if "tile32" in case else "tma"
+        m = torch.randn(side, side, device="cuda").to(dt)
+        o = torch.empty(side, side, device="cuda", dtype=dt)
+        for _ in range(args.case_reps):
+            api.transpose(m, out=o, kernel=kernel)
+    elif case.startswith("reduce"):
+        dt = torch.bfloat16 if "bf16" in case else torch.float32
+        v = torch.randn(side * side, device="cuda").to(dt)
+        r = torch.empty((), dtype=torch.float64, device="cuda")
+        for _ in range(args.case_reps):
+            api.reduce_sum(v, out=r, compensated=case.endswith("comp"))
+    elif case == "batch":
+        inst = workloads.batched_instances(count=args.count)
+        data = workloads.batched_data(inst)
+        items = []
+        for i, a in zip(inst, data):
+            d = torch.from_numpy(a).cuda()
+            if i.op == 0:
+                items.append(("transpose", d, torch.empty((i.cols, i.rows), device="cuda")))
+            else:
+                items.append(("reduce", d, torch.empty((), dtype=torch.float64, device="cuda")))
+        plan = api.BatchPlan(items)
+        for _ in range(args.case_reps):
+            plan.run()
+        torch.cuda.synchronize()
+        plan.close()
+    else:
+        raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize()
+    api.stream_status()
+    print(f"case {case} side {side} reps {args.case_reps}: ok")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,7 +544,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
+                         "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch)")
+    ap.add_argument("--side", type=int, default=8192)
+    ap.add_argument("--count", type=int, default=1024)
+    ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
