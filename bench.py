@@ -325,6 +325,57 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
     return res
 
 
+def measure_precision():
+    """The precision workload: 2^28 N(100,1) values rounded to bf16 and to
+    fp16 (seed 2), summed in FP32 plain and compensated with the FP64 final
+    combine; errors against the exact FP64 oracle.  Plus the 8192x8192 bf16
+    transpose, checked bit-exact."""
+    import torch
+    import oracle
+    from paper_2605_13864_gb300 import api, workloads
+
+    vb, vh = workloads.precision_vectors()
+    res = {"workload": "2^28 N(100,1) rounded to bf16 / fp16 (seed 2); bf16 8192x8192 N(0,1) transpose"}
+    for name, v, tdt in (("bf16", vb, torch.bfloat16), ("fp16", vh, torch.float16)):
+        ref = oracle.reduce_reference(v, "bfloat16" if name == "bf16" else "float16")
+        d = torch.from_numpy(v.view(np.int16)).view(tdt).cuda()
+        out = torch.empty((), dtype=torch.float64, device="cuda")
+        for comp in (False, True):
+            api.reduce_sum(d, out=out, compensated=comp)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(20):
+                api.reduce_sum(d, out=out, compensated=comp)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 20
+            got = out.item()
+            err = abs(got - ref["f64"])
+            res[f"{name}_{'compensated' if comp else 'plain'}"] = {
+                "sum": got, "oracle_fp64": ref["f64"], "abs_error": err,
+                "rel_error_vs_sum_abs": err / ref["abs"], "within_1e-6": err <= 1e-6 * ref["abs"],
+                "ms": round(ms, 4), "gbs": round(v.nbytes / ms / 1e6, 1)}
+        del d
+    m = workloads.precision_matrix()
+    d = torch.from_numpy(m.view(np.int16)).view(torch.bfloat16).cuda()
+    o = api.transpose(d)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(20):
+        api.transpose(d, out=o)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 20
+    exact = np.array_equal(o.view(torch.int16).cpu().numpy().view(np.uint16), oracle.transpose(m))
+    res["bf16_transpose_8192"] = {"bit_exact": bool(exact), "ms": round(ms, 4),
+                                  "gbs": round(2 * m.nbytes / ms / 1e6, 1)}
+    del d, o
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -425,14 +476,16 @@ def run_gpu(args):
     out_tp = torch.empty((COLS, ROWS), dtype=torch.float32).pin_memory()
     del mat, vec, out_t
     torch.cuda.empty_cache()
+    out_rp = torch.empty((), dtype=torch.float64).pin_memory()
     api.transpose(mat_p, out=out_tp)
-    api.reduce_sum(vec_p)
+    api.reduce_sum(vec_p, out=out_rp)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(3, min(args.steps, 10))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        api.transpose(mat_p, out=out_tp)
-        api.reduce_sum(vec_p).item()
+        api.transpose(mat_p, out=out_tp)      # host buffers: copies inside the call
+        api.reduce_sum(vec_p, out=out_rp)
+        float(out_rp.item())
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
@@ -481,6 +534,8 @@ def run_gpu(args):
             line["batched"] = measure_batched()
         if not args.no_served:
             line["served"] = measure_served()
+        if not args.no_precision:
+            line["precision"] = measure_precision()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -544,6 +599,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch)")

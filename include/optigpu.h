@@ -182,6 +182,34 @@ optigpu_status optigpu_reduce_sum_noalloc(const void *src, int64_t n,
                                           optigpu_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Host buffers: the same operations with the copies pipelined              */
+/* ------------------------------------------------------------------------ */
+/* The thesis's host code copies the whole input in, launches and copies the
+ * result back (Listings 3.6, 3.11).  These entry points take HOST pointers
+ * and cut the work into row bands (transpose) or chunk bands (sum) that
+ * alternate between two internal streams, so copies in, kernels and copies
+ * out overlap.  Results are identical to the device-buffer calls (the sum is
+ * bit-identical to optigpu_reduce_sum_ex).  Pinned host memory
+ * (cudaHostAlloc / cudaHostRegister) makes the copies asynchronous; pageable
+ * memory works but copies synchronously.  The calls are asynchronous on
+ * `stream`: host buffers must stay valid and untouched until it completes.
+ * Device staging buffers (2 x 2 x ~64 MiB) are library-owned, cudaMalloc'd on
+ * first use per device and reused; do not call during stream capture. */
+
+/* host_dst (cols x rows) = transpose of host_src (rows x cols), both dense
+ * row-major in host memory.  Errors as optigpu_transpose (OVERLAP for
+ * overlapping host ranges). */
+optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int64_t rows,
+                                      int64_t cols, optigpu_dtype dtype,
+                                      optigpu_stream_t stream);
+
+/* *host_out (8 bytes: int64 or double) = sum of host_src[0 .. n).  Errors as
+ * optigpu_reduce_sum_ex. */
+optigpu_status optigpu_reduce_sum_host(const void *host_src, int64_t n, optigpu_dtype dtype,
+                                       void *host_out, uint32_t flags,
+                                       optigpu_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batches: many uneven transposes and sums in one persistent launch        */
 /* ------------------------------------------------------------------------ */
 /* The thesis launches one kernel per problem (Listings 3.6, 6.21).  A batch

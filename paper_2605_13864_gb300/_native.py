@@ -49,6 +49,8 @@ SIGNATURES = {
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_reserve": (_ci, [_i64, _vp]),
+    "optigpu_transpose_host": (_ci, [_vp, _vp, _i64, _i64, _ci, _vp]),
+    "optigpu_reduce_sum_host": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_batch_plan_create": (_ci, [_vp, ctypes.c_int32, _u32, ctypes.POINTER(_vp)]),
     "optigpu_batch_run": (_ci, [_vp, _vp]),
     "optigpu_batch_plan_info": (_ci, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),

@@ -35,13 +35,19 @@ def transpose(src: torch.Tensor, out: torch.Tensor | None = None, kernel: str = 
     if src.dim() != 2:
         raise ValueError("transpose expects a 2-D tensor")
     if not src.is_cuda:
-        dev = torch.device("cuda", torch.cuda.current_device())
-        d_src = src.to(dev, non_blocking=True)
-        d_out = transpose(d_src, kernel=kernel, stream=stream)
-        host = out if out is not None else torch.empty(
-            (src.shape[1], src.shape[0]), dtype=src.dtype, pin_memory=True)
-        host.copy_(d_out, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        # Host buffers: the library pipelines copy-in, kernel and copy-out.
+        if not src.is_contiguous():
+            raise ValueError("transpose expects a contiguous (row-major) source")
+        rows, cols = src.shape
+        host = out if out is not None else torch.empty((cols, rows), dtype=src.dtype, pin_memory=True)
+        if host.is_cuda or tuple(host.shape) != (cols, rows) or not host.is_contiguous():
+            raise ValueError("out must be a contiguous host (cols, rows) tensor")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        st = N.lib().optigpu_transpose_host(src.data_ptr() if src.numel() else None,
+                                            host.data_ptr() if host.numel() else None, rows, cols,
+                                            dtype_code(src.dtype), int(s.cuda_stream))
+        N.check(st, "optigpu_transpose_host")
+        s.synchronize()
         return host
     if not src.is_contiguous():
         raise ValueError("transpose expects a contiguous (row-major) source")
@@ -64,9 +70,17 @@ def reduce_sum(x: torch.Tensor, compensated: bool = False, out: torch.Tensor | N
     float input (the partials are combined in FP64 on the GPU).
     """
     if not x.is_cuda:
-        dev = torch.device("cuda", torch.cuda.current_device())
-        d = reduce_sum(x.to(dev, non_blocking=True), compensated=compensated, stream=stream)
-        res = d.to("cpu")
+        # Host buffer: the library pipelines the copy-in against the partials.
+        if not x.is_contiguous():
+            raise ValueError("reduce_sum expects a contiguous tensor")
+        odt = torch.int64 if x.dtype == torch.int32 else torch.float64
+        res = out if out is not None else torch.empty((), dtype=odt, pin_memory=True)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        flags = N.REDUCE_COMPENSATED if compensated else N.REDUCE_PLAIN
+        st = N.lib().optigpu_reduce_sum_host(x.data_ptr() if x.numel() else None, x.numel(),
+                                             dtype_code(x.dtype), res.data_ptr(), flags, int(s.cuda_stream))
+        N.check(st, "optigpu_reduce_sum_host")
+        s.synchronize()
         return res
     if not x.is_contiguous():
         raise ValueError("reduce_sum expects a contiguous tensor")

@@ -1,0 +1,260 @@
+// host_io.cu -- the transpose and the sum on HOST buffers, with the copies
+// pipelined against the kernels.
+//
+// The thesis's host code copies the whole input in, launches, and copies the
+// whole result back (Listings 3.6, 3.11).  Here the input is cut into row
+// bands that alternate between two internal streams and two pairs of device
+// staging buffers, so band k+1's host->device copy overlaps band k's kernel
+// and band k-1's device->host copy (the two copy directions run on separate
+// copy engines).
+//
+//  transpose  band k = rows [k*B, k*B + b) of src is itself a b x cols matrix;
+//             its transpose (cols x b) is the column band [k*B, k*B + b) of
+//             dst and goes back with one strided 2-D copy.
+//  sum        bands are whole chunks (B multiple of 16384 elements); each band
+//             writes the partials of its chunks into one array, and one final
+//             combine runs when every band is in.  The partials and the
+//             combine are the single-pass kernel's, so the result is
+//             bit-identical to optigpu_reduce_sum_ex on device memory.
+//
+// Calls are asynchronous on the caller's stream (the internal streams wait
+// for it and it waits for them); the staging buffers are library-owned, per
+// device, and reused by the next call in stream order.
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+#include "reduce_core.cuh"
+
+namespace optigpu {
+namespace {
+
+constexpr size_t kBandBytes = size_t(64) << 20; // target bytes per band
+
+struct HostIo {
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, done[2] = {nullptr, nullptr};
+    void *in[2] = {nullptr, nullptr};
+    void *out[2] = {nullptr, nullptr};
+    size_t cap = 0; // bytes of each staging buffer
+    void *partials = nullptr;
+    size_t partial_cap = 0;
+    void *result = nullptr; // one 8-byte device result
+    bool joined = false;    // done[] hold the end of a previous call
+};
+
+std::mutex g_io_mu;
+std::map<int, HostIo> g_io;
+
+optigpu_status get_io(HostIo *&io, size_t band_bytes)
+{
+    int dev = -1;
+    optigpu_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != OPTIGPU_OK)
+        return st;
+    HostIo &h = g_io[dev];
+    if (!h.s[0]) {
+        for (int i = 0; i < 2; ++i) {
+            if ((st = check_cuda(cudaStreamCreateWithFlags(&h.s[i], cudaStreamNonBlocking), "host io: stream")) !=
+                OPTIGPU_OK)
+                return st;
+            if ((st = check_cuda(cudaEventCreateWithFlags(&h.done[i], cudaEventDisableTiming), "host io: event")) !=
+                OPTIGPU_OK)
+                return st;
+        }
+        if ((st = check_cuda(cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming), "host io: event")) !=
+            OPTIGPU_OK)
+            return st;
+        if ((st = check_cuda(cudaMalloc(&h.result, 256), "host io: cudaMalloc(result)")) != OPTIGPU_OK)
+            return st;
+    }
+    if (h.cap < band_bytes) {
+        // Earlier calls may still use the buffers.
+        for (int i = 0; i < 2; ++i)
+            if ((st = check_cuda(cudaStreamSynchronize(h.s[i]), "host io: sync")) != OPTIGPU_OK)
+                return st;
+        for (int i = 0; i < 2; ++i) {
+            if (h.in[i])
+                cudaFree(h.in[i]);
+            if (h.out[i])
+                cudaFree(h.out[i]);
+            h.in[i] = h.out[i] = nullptr;
+        }
+        h.cap = 0;
+        for (int i = 0; i < 2; ++i) {
+            if ((st = check_cuda(cudaMalloc(&h.in[i], band_bytes), "host io: cudaMalloc(staging)")) != OPTIGPU_OK)
+                return st;
+            if ((st = check_cuda(cudaMalloc(&h.out[i], band_bytes), "host io: cudaMalloc(staging)")) != OPTIGPU_OK)
+                return st;
+        }
+        h.cap = band_bytes;
+    }
+    io = &h;
+    return OPTIGPU_OK;
+}
+
+// The internal streams wait for the caller's stream; the caller's stream will
+// wait for both internal streams at the end.
+// Each internal stream also waits for the other's end of the previous call,
+// so a call never overwrites staging or partials that the previous call
+// (possibly issued on another caller stream) still reads.
+optigpu_status fork(HostIo &h, cudaStream_t user)
+{
+    optigpu_status st = check_cuda(cudaEventRecord(h.start, user), "host io: record");
+    for (int i = 0; i < 2 && st == OPTIGPU_OK; ++i) {
+        st = check_cuda(cudaStreamWaitEvent(h.s[i], h.start, 0), "host io: wait");
+        if (st == OPTIGPU_OK && h.joined)
+            st = check_cuda(cudaStreamWaitEvent(h.s[i], h.done[1 - i], 0), "host io: wait");
+    }
+    return st;
+}
+
+optigpu_status join(HostIo &h, cudaStream_t user)
+{
+    optigpu_status st = OPTIGPU_OK;
+    for (int i = 0; i < 2 && st == OPTIGPU_OK; ++i) {
+        st = check_cuda(cudaEventRecord(h.done[i], h.s[i]), "host io: record");
+        if (st == OPTIGPU_OK)
+            st = check_cuda(cudaStreamWaitEvent(user, h.done[i], 0), "host io: wait");
+    }
+    h.joined = (st == OPTIGPU_OK);
+    return st;
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+} // namespace
+} // namespace optigpu
+
+using namespace optigpu;
+
+extern "C" {
+
+optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int64_t rows, int64_t cols,
+                                      optigpu_dtype dtype, optigpu_stream_t stream)
+{
+    if (!dtype_valid(int(dtype)))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_host: unknown dtype");
+    if (rows < 0 || cols < 0)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_host: negative rows or cols");
+    if (rows == 0 || cols == 0)
+        return OPTIGPU_OK;
+    const size_t es = esize_of(dtype);
+    if (rows > (int64_t(1) << 62) / cols || rows * cols > (int64_t(1) << 62) / int64_t(es))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_host: rows * cols * element size too large");
+    if (!host_src || !host_dst)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_host: null pointer");
+    const size_t bytes = size_t(rows) * size_t(cols) * es;
+    if (ranges_overlap(host_src, bytes, host_dst, bytes))
+        return fail(OPTIGPU_ERR_OVERLAP, "transpose_host: src and dst overlap");
+    // Band height: a multiple of 64 rows near kBandBytes when rows are short,
+    // else as many whole rows as fit (at least one).
+    const size_t row_bytes = size_t(cols) * es;
+    const size_t fit = kBandBytes / row_bytes;
+    int64_t band = int64_t(fit >= 64 ? fit / 64 * 64 : std::max<size_t>(fit, 1));
+    band = std::min<int64_t>(band, rows);
+    std::lock_guard<std::mutex> lk(g_io_mu);
+    HostIo *io = nullptr;
+    optigpu_status st = get_io(io, size_t(band) * row_bytes);
+    if (st != OPTIGPU_OK)
+        return st;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if ((st = fork(*io, user)) != OPTIGPU_OK)
+        return st;
+    const char *src = static_cast<const char *>(host_src);
+    char *dst = static_cast<char *>(host_dst);
+    for (int64_t k = 0, r0 = 0; r0 < rows; ++k, r0 += band) {
+        const int64_t b = std::min<int64_t>(band, rows - r0);
+        const int i = int(k & 1);
+        cudaStream_t s = io->s[i];
+        if ((st = check_cuda(cudaMemcpyAsync(io->in[i], src + size_t(r0) * row_bytes, size_t(b) * row_bytes,
+                                             cudaMemcpyHostToDevice, s),
+                             "transpose_host: copy in")) != OPTIGPU_OK)
+            return st;
+        if ((st = transpose_dispatch(io->in[i], io->out[i], b, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO, s)) !=
+            OPTIGPU_OK)
+            return st;
+        // dst[c][r0 .. r0+b) for every c: a cols-high, b*es-wide strided block.
+        if ((st = check_cuda(cudaMemcpy2DAsync(dst + size_t(r0) * es, size_t(rows) * es, io->out[i], size_t(b) * es,
+                                               size_t(b) * es, size_t(cols), cudaMemcpyDeviceToHost, s),
+                             "transpose_host: copy out")) != OPTIGPU_OK)
+            return st;
+    }
+    return join(*io, user);
+}
+
+optigpu_status optigpu_reduce_sum_host(const void *host_src, int64_t n, optigpu_dtype dtype, void *host_out,
+                                       uint32_t flags, optigpu_stream_t stream)
+{
+    if (!dtype_valid(int(dtype)))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce_sum_host: unknown dtype");
+    if (flags & ~OPTIGPU_REDUCE_COMPENSATED)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_host: unknown flag bits");
+    if (n < 0 || n > (int64_t(1) << 62))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_host: n out of range");
+    if (!host_out || (n > 0 && !host_src))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_host: null pointer");
+    const size_t es = esize_of(dtype);
+    if (n > 0 && reinterpret_cast<uintptr_t>(host_src) % es)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_host: src not aligned to the element size");
+    // Band: whole chunks near kBandBytes.
+    const int64_t chunk_bytes = kReduceChunk * int64_t(es);
+    const int64_t band = std::max<int64_t>(1, int64_t(kBandBytes) / chunk_bytes) * kReduceChunk;
+    const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
+    std::lock_guard<std::mutex> lk(g_io_mu);
+    HostIo *io = nullptr;
+    optigpu_status st = get_io(io, size_t(std::min<int64_t>(band, std::max<int64_t>(n, 1))) * es);
+    if (st != OPTIGPU_OK)
+        return st;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if (io->partial_cap < size_t(num_chunks) * 8) {
+        for (int i = 0; i < 2; ++i)
+            if ((st = check_cuda(cudaStreamSynchronize(io->s[i]), "host io: sync")) != OPTIGPU_OK)
+                return st;
+        if (io->partials)
+            cudaFree(io->partials);
+        io->partials = nullptr;
+        io->partial_cap = 0;
+        const size_t want = std::max<size_t>(size_t(num_chunks) * 8, 4096);
+        if ((st = check_cuda(cudaMalloc(&io->partials, want), "host io: cudaMalloc(partials)")) != OPTIGPU_OK)
+            return st;
+        io->partial_cap = want;
+    }
+    if ((st = fork(*io, user)) != OPTIGPU_OK)
+        return st;
+    if (n == 0) {
+        if ((st = check_cuda(cudaMemsetAsync(io->result, 0, 8, io->s[0]), "reduce_sum_host: zero")) != OPTIGPU_OK)
+            return st;
+    } else {
+        const char *src = static_cast<const char *>(host_src);
+        for (int64_t k = 0, e0 = 0; e0 < n; ++k, e0 += band) {
+            const int64_t b = std::min<int64_t>(band, n - e0);
+            const int i = int(k & 1);
+            if ((st = check_cuda(cudaMemcpyAsync(io->in[i], src + size_t(e0) * es, size_t(b) * es,
+                                                 cudaMemcpyHostToDevice, io->s[i]),
+                                 "reduce_sum_host: copy in")) != OPTIGPU_OK)
+                return st;
+            if ((st = reduce_band(io->in[i], b, int(dtype), flags, io->partials, e0 / kReduceChunk, io->s[i])) !=
+                OPTIGPU_OK)
+                return st;
+        }
+        // The final combine needs every band: stream 0 waits for stream 1.
+        if ((st = check_cuda(cudaEventRecord(io->done[1], io->s[1]), "host io: record")) != OPTIGPU_OK)
+            return st;
+        if ((st = check_cuda(cudaStreamWaitEvent(io->s[0], io->done[1], 0), "host io: wait")) != OPTIGPU_OK)
+            return st;
+        if ((st = reduce_final(io->partials, num_chunks, int(dtype), flags, io->result, io->s[0])) != OPTIGPU_OK)
+            return st;
+    }
+    if ((st = check_cuda(cudaMemcpyAsync(host_out, io->result, 8, cudaMemcpyDeviceToHost, io->s[0]),
+                         "reduce_sum_host: copy out")) != OPTIGPU_OK)
+        return st;
+    return join(*io, user);
+}
+
+} // extern "C"

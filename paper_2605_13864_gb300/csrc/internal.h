@@ -77,6 +77,16 @@ void reduce_select(int config);
 optigpu_status reduce_dispatch(const void *src, int64_t n, int dtype, void *out, uint32_t flags,
                                cudaStream_t stream);
 
+// Partials of the chunks of one band (band_src = chunk `chunk_base`'s first
+// element, band_n elements) into partials[chunk_base ...], and the final
+// combine of `count` partials into *out: together, the single-pass sum.
+optigpu_status reduce_band(const void *band_src, int64_t band_n, int dtype, uint32_t flags, void *partials,
+                           int64_t chunk_base, cudaStream_t stream);
+optigpu_status reduce_final(const void *partials, int64_t count, int dtype, uint32_t flags, void *out,
+                            cudaStream_t stream);
+optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
+                                  cudaStream_t stream);
+
 // Batch kernel configurations (default of new plans).
 int batch_num_configs();
 const char *batch_config_name(int config);

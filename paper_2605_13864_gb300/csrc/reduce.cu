@@ -78,6 +78,33 @@ constexpr const char *kReduceConfigNames[] = {"reduce ctas/SM=max", "reduce ctas
                                               "reduce ctas/SM=4", "reduce ctas/SM=6"};
 std::atomic<int> g_reduce_choice{0};
 
+// Partials only, for a band of a larger input: chunk c of the band is
+// chunk (chunk_base + c) of the whole vector, and band_src starts at that
+// chunk's first element, so each partial is the one the single-pass kernel
+// computes.
+template <int DT, bool COMP>
+__global__ void __launch_bounds__(kReduceThreads)
+reduce_band_kernel(const void *__restrict__ band_src, int64_t band_n, int vec_ok, void *partials, int64_t chunk_base,
+                   int64_t band_chunks)
+{
+    using Core = ReduceCore<DT, COMP>;
+    __shared__ typename Core::Shared sh;
+    for (int64_t c = blockIdx.x; c < band_chunks; c += gridDim.x) {
+        const auto part = Core::chunk_partial(band_src, band_n, c, vec_ok != 0, sh);
+        if (threadIdx.x == 0)
+            Core::store_partial(partials, chunk_base + c, part);
+    }
+}
+
+// The final combine alone (one CTA).
+template <int DT, bool COMP>
+__global__ void __launch_bounds__(kReduceThreads) reduce_final_kernel(const void *partials, int64_t count, void *out)
+{
+    using Core = ReduceCore<DT, COMP>;
+    __shared__ typename Core::Shared sh;
+    Core::final_combine(partials, count, out, sh);
+}
+
 struct KernelFacts {
     bool ready = false;
     int ctas_per_sm = 0;
@@ -125,7 +152,66 @@ optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream
     return check_cuda(cudaGetLastError(), "launch reduce");
 }
 
+template <int DT, bool COMP>
+optigpu_status launch_band(const void *band_src, int64_t band_n, void *partials, int64_t chunk_base,
+                           cudaStream_t stream)
+{
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const int64_t chunks = (band_n + kReduceChunk - 1) / kReduceChunk;
+    const int64_t grid = std::min<int64_t>(chunks, int64_t(8) * dev.num_sms);
+    const int vec_ok = (reinterpret_cast<uintptr_t>(band_src) & 15u) == 0 ? 1 : 0;
+    reduce_band_kernel<DT, COMP><<<unsigned(std::max<int64_t>(grid, 1)), kReduceThreads, 0, stream>>>(
+        band_src, band_n, vec_ok, partials, chunk_base, chunks);
+    return check_cuda(cudaGetLastError(), "launch reduce band");
+}
+
+template <int DT, bool COMP>
+optigpu_status launch_final(const void *partials, int64_t count, void *out, cudaStream_t stream)
+{
+    reduce_final_kernel<DT, COMP><<<1, kReduceThreads, 0, stream>>>(partials, count, out);
+    return check_cuda(cudaGetLastError(), "launch reduce final");
+}
+
 } // namespace
+
+optigpu_status reduce_band(const void *band_src, int64_t band_n, int dtype, uint32_t flags, void *partials,
+                           int64_t chunk_base, cudaStream_t stream)
+{
+    const bool comp = (flags & OPTIGPU_REDUCE_COMPENSATED) != 0;
+    switch (dtype) {
+    case OPTIGPU_INT32: return launch_band<OPTIGPU_INT32, false>(band_src, band_n, partials, chunk_base, stream);
+    case OPTIGPU_FLOAT32:
+        return comp ? launch_band<OPTIGPU_FLOAT32, true>(band_src, band_n, partials, chunk_base, stream)
+                    : launch_band<OPTIGPU_FLOAT32, false>(band_src, band_n, partials, chunk_base, stream);
+    case OPTIGPU_BFLOAT16:
+        return comp ? launch_band<OPTIGPU_BFLOAT16, true>(band_src, band_n, partials, chunk_base, stream)
+                    : launch_band<OPTIGPU_BFLOAT16, false>(band_src, band_n, partials, chunk_base, stream);
+    default:
+        return comp ? launch_band<OPTIGPU_FLOAT16, true>(band_src, band_n, partials, chunk_base, stream)
+                    : launch_band<OPTIGPU_FLOAT16, false>(band_src, band_n, partials, chunk_base, stream);
+    }
+}
+
+optigpu_status reduce_final(const void *partials, int64_t count, int dtype, uint32_t flags, void *out,
+                            cudaStream_t stream)
+{
+    const bool comp = (flags & OPTIGPU_REDUCE_COMPENSATED) != 0;
+    switch (dtype) {
+    case OPTIGPU_INT32: return launch_final<OPTIGPU_INT32, false>(partials, count, out, stream);
+    case OPTIGPU_FLOAT32:
+        return comp ? launch_final<OPTIGPU_FLOAT32, true>(partials, count, out, stream)
+                    : launch_final<OPTIGPU_FLOAT32, false>(partials, count, out, stream);
+    case OPTIGPU_BFLOAT16:
+        return comp ? launch_final<OPTIGPU_BFLOAT16, true>(partials, count, out, stream)
+                    : launch_final<OPTIGPU_BFLOAT16, false>(partials, count, out, stream);
+    default:
+        return comp ? launch_final<OPTIGPU_FLOAT16, true>(partials, count, out, stream)
+                    : launch_final<OPTIGPU_FLOAT16, false>(partials, count, out, stream);
+    }
+}
 
 int reduce_num_configs() { return int(sizeof(kReduceCtasPerSm) / sizeof(kReduceCtasPerSm[0])); }
 

@@ -35,10 +35,6 @@
 #include "reduce_core.cuh"
 
 namespace optigpu {
-
-optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
-                                  cudaStream_t stream);
-
 namespace {
 
 double now_s()

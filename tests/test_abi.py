@@ -192,3 +192,14 @@ def test_server_validation_is_host_side(lib):
     assert lib.optigpu_server_drain(None) == N.ERR_INVALID_ARG
     assert lib.optigpu_server_replay(None, None, None, 1, None) == N.ERR_INVALID_ARG
     lib.optigpu_server_destroy(None)
+
+
+def test_host_entry_points_validate_on_the_host(lib):
+    assert lib.optigpu_transpose_host(None, None, -1, 3, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_transpose_host(FAKE, FAKE + 8, 4, 4, N.FLOAT32, None) == N.ERR_OVERLAP
+    assert lib.optigpu_transpose_host(None, None, 0, 3, N.FLOAT32, None) == N.OK
+    assert lib.optigpu_transpose_host(FAKE, FAKE + (1 << 20), 4, 4, 11, None) == N.ERR_UNSUPPORTED_DTYPE
+    assert lib.optigpu_reduce_sum_host(None, 5, N.FLOAT32, FAKE, 0, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_reduce_sum_host(FAKE, 5, N.FLOAT32, None, 0, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_reduce_sum_host(FAKE + 2, 5, N.FLOAT32, FAKE, 0, None) == N.ERR_INVALID_ARG
+    assert lib.optigpu_reduce_sum_host(FAKE, 5, N.FLOAT32, FAKE, 8, None) == N.ERR_INVALID_ARG
