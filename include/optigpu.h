@@ -111,6 +111,15 @@ optigpu_status optigpu_transpose_ex(const void *src, void *dst, int64_t rows,
                                     optigpu_transpose_kernel kernel,
                                     optigpu_stream_t stream);
 
+/* Pitched transpose: dst[c * ldd + r] = src[r * lds + c] for r < rows,
+ * c < cols (row pitches lds >= cols and ldd >= rows, in elements), so either
+ * matrix may be a sub-block of a larger row-major array.  Same kernels (TMA
+ * when pointers are 16-byte aligned and rows, cols, lds, ldd are multiples of
+ * 16 / element size), same errors (OVERLAP on the touched byte spans). */
+optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst, int64_t ldd,
+                                         int64_t rows, int64_t cols, optigpu_dtype dtype,
+                                         optigpu_stream_t stream);
+
 /* 1 if the TMA kernel accepts this shape and these pointers, else 0. */
 int optigpu_transpose_tma_eligible(const void *src, const void *dst,
                                    int64_t rows, int64_t cols,

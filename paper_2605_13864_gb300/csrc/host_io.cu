@@ -1,21 +1,25 @@
-// host_io.cu -- the transpose and the sum on HOST buffers, with the copies
-// pipelined against the kernels.
+// host_io.cu -- the transpose and the sum on HOST buffers.
 //
 // The thesis's host code copies the whole input in, launches, and copies the
-// whole result back (Listings 3.6, 3.11).  Here the input is cut into row
-// bands that alternate between two internal streams and two pairs of device
-// staging buffers, so band k+1's host->device copy overlaps band k's kernel
-// and band k-1's device->host copy (the two copy directions run on separate
-// copy engines).
+// whole result back (Listings 3.6, 3.11).  On Grace-Blackwell the GPU reaches
+// pinned host memory directly over NVLink-C2C, so for pinned buffers the
+// kernels read and write host memory themselves ("zero-copy"): one launch, no
+// staging, both link directions busy at once.  Which buffers qualify is
+// checked with cudaPointerGetAttributes (page-locked host memory with a
+// device mapping, at both ends of the range); only the SIMT kernels touch
+// host memory, never TMA.
 //
-//  transpose  band k = rows [k*B, k*B + b) of src is itself a b x cols matrix;
-//             its transpose (cols x b) is the column band [k*B, k*B + b) of
-//             dst and goes back with one strided 2-D copy.
+// Pageable buffers are staged through device memory instead, with every copy
+// contiguous (strided 2-D copies with short rows run far below link speed):
+//  transpose  row bands of src alternate between two internal streams and
+//             two staging buffers, so band k+1's copy in overlaps band k's
+//             transpose, which writes the column band [k*B, k*B + b) of a
+//             full-size device dst; one copy brings dst back at the end.
 //  sum        bands are whole chunks (B multiple of 16384 elements); each band
 //             writes the partials of its chunks into one array, and one final
-//             combine runs when every band is in.  The partials and the
-//             combine are the single-pass kernel's, so the result is
-//             bit-identical to optigpu_reduce_sum_ex on device memory.
+//             combine runs when every band is in.
+// Either way the partials and the combine are the single-pass kernel's, so
+// the sum is bit-identical to optigpu_reduce_sum_ex on device memory.
 //
 // Calls are asynchronous on the caller's stream (the internal streams wait
 // for it and it waits for them); the staging buffers are library-owned, per
@@ -41,6 +45,8 @@ struct HostIo {
     void *partials = nullptr;
     size_t partial_cap = 0;
     void *result = nullptr; // one 8-byte device result
+    void *full = nullptr;   // full-size device dst of a staged transpose
+    size_t full_cap = 0;
     bool joined = false;    // done[] hold the end of a previous call
 };
 
@@ -122,6 +128,31 @@ optigpu_status join(HostIo &h, cudaStream_t user)
     return st;
 }
 
+// Device address of host memory [p, p + bytes) if it is page-locked and
+// mapped for the device (both ends checked), else nullptr.
+void *device_view_of_host(const void *p, size_t bytes)
+{
+    if (!p || bytes == 0)
+        return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+        return nullptr;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    cudaPointerAttributes b{};
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<char *>(b.devicePointer) != static_cast<char *>(a.devicePointer) + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
 bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
 {
     const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -152,8 +183,13 @@ optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int6
     const size_t bytes = size_t(rows) * size_t(cols) * es;
     if (ranges_overlap(host_src, bytes, host_dst, bytes))
         return fail(OPTIGPU_ERR_OVERLAP, "transpose_host: src and dst overlap");
-    // Band height: a multiple of 64 rows near kBandBytes when rows are short,
-    // else as many whole rows as fit (at least one).
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    void *zsrc = device_view_of_host(host_src, bytes);
+    void *zdst = device_view_of_host(host_dst, bytes);
+    if (zsrc && zdst)
+        return transpose_dispatch(zsrc, zdst, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_TILE32, user);
+    // Staged: band height a multiple of 64 rows near kBandBytes when rows are
+    // short, else as many whole rows as fit (at least one).
     const size_t row_bytes = size_t(cols) * es;
     const size_t fit = kBandBytes / row_bytes;
     int64_t band = int64_t(fit >= 64 ? fit / 64 * 64 : std::max<size_t>(fit, 1));
@@ -163,11 +199,22 @@ optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int6
     optigpu_status st = get_io(io, size_t(band) * row_bytes);
     if (st != OPTIGPU_OK)
         return st;
-    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if (io->full_cap < bytes) {
+        for (int i = 0; i < 2; ++i)
+            if ((st = check_cuda(cudaStreamSynchronize(io->s[i]), "host io: sync")) != OPTIGPU_OK)
+                return st;
+        if (io->full)
+            cudaFree(io->full);
+        io->full = nullptr;
+        io->full_cap = 0;
+        if ((st = check_cuda(cudaMalloc(&io->full, bytes), "host io: cudaMalloc(dst)")) != OPTIGPU_OK)
+            return st;
+        io->full_cap = bytes;
+    }
     if ((st = fork(*io, user)) != OPTIGPU_OK)
         return st;
     const char *src = static_cast<const char *>(host_src);
-    char *dst = static_cast<char *>(host_dst);
+    char *full = static_cast<char *>(io->full);
     for (int64_t k = 0, r0 = 0; r0 < rows; ++k, r0 += band) {
         const int64_t b = std::min<int64_t>(band, rows - r0);
         const int i = int(k & 1);
@@ -176,15 +223,20 @@ optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int6
                                              cudaMemcpyHostToDevice, s),
                              "transpose_host: copy in")) != OPTIGPU_OK)
             return st;
-        if ((st = transpose_dispatch(io->in[i], io->out[i], b, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO, s)) !=
+        // The band's transpose is dst[:, r0 .. r0 + b): written in place with
+        // the padded tile kernel on a view whose row pitch is `rows`.
+        if ((st = transpose_band_into(io->in[i], full + size_t(r0) * es, b, cols, rows, int(dtype), s)) !=
             OPTIGPU_OK)
             return st;
-        // dst[c][r0 .. r0+b) for every c: a cols-high, b*es-wide strided block.
-        if ((st = check_cuda(cudaMemcpy2DAsync(dst + size_t(r0) * es, size_t(rows) * es, io->out[i], size_t(b) * es,
-                                               size_t(b) * es, size_t(cols), cudaMemcpyDeviceToHost, s),
-                             "transpose_host: copy out")) != OPTIGPU_OK)
-            return st;
     }
+    // Every band must be in before dst goes back in one contiguous copy.
+    if ((st = check_cuda(cudaEventRecord(io->done[1], io->s[1]), "host io: record")) != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaStreamWaitEvent(io->s[0], io->done[1], 0), "host io: wait")) != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaMemcpyAsync(host_dst, full, bytes, cudaMemcpyDeviceToHost, io->s[0]),
+                         "transpose_host: copy out")) != OPTIGPU_OK)
+        return st;
     return join(*io, user);
 }
 
@@ -202,6 +254,11 @@ optigpu_status optigpu_reduce_sum_host(const void *host_src, int64_t n, optigpu_
     const size_t es = esize_of(dtype);
     if (n > 0 && reinterpret_cast<uintptr_t>(host_src) % es)
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_sum_host: src not aligned to the element size");
+    cudaStream_t user0 = static_cast<cudaStream_t>(stream);
+    void *zsrc = device_view_of_host(host_src, size_t(n) * es);
+    void *zout = device_view_of_host(host_out, 8);
+    if ((zsrc || n == 0) && zout)
+        return reduce_dispatch(zsrc, n, int(dtype), zout, flags, user0);
     // Band: whole chunks near kBandBytes.
     const int64_t chunk_bytes = kReduceChunk * int64_t(es);
     const int64_t band = std::max<int64_t>(1, int64_t(kBandBytes) / chunk_bytes) * kReduceChunk;

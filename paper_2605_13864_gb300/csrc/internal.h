@@ -86,6 +86,12 @@ optigpu_status reduce_final(const void *partials, int64_t count, int dtype, uint
                             cudaStream_t stream);
 optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
                                   cudaStream_t stream);
+// Same with row pitches: dst[c * ldd + r] = src[r * lds + c].
+optigpu_status transpose_dispatch_pitched(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t rows,
+                                          int64_t cols, int dtype, int kernel, cudaStream_t stream);
+// Transpose of a dense b x cols band into dst with row pitch ldd.
+optigpu_status transpose_band_into(const void *band, void *dst, int64_t b, int64_t cols, int64_t ldd, int dtype,
+                                   cudaStream_t stream);
 
 // Batch kernel configurations (default of new plans).
 int batch_num_configs();

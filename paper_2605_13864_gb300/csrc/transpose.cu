@@ -46,7 +46,7 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256)
 transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t rows,
-                        int64_t cols, int64_t tiles_c)
+                        int64_t cols, int64_t tiles_c, int64_t lds, int64_t ldd)
 {
     // 4-byte rows are padded by one element, 2-byte rows by two, so that a
     // column of the tile spans 32 distinct 4-byte banks.
@@ -61,14 +61,14 @@ transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t 
     for (int j = 0; j < 32; j += 8) {
         const int64_t r = r0 + y + j, c = c0 + x;
         if (r < rows && c < cols)
-            tile[y + j][x] = src[r * cols + c];
+            tile[y + j][x] = src[r * lds + c];
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 32; j += 8) {
         const int64_t orow = c0 + y + j, ocol = r0 + x;
         if (orow < cols && ocol < rows)
-            dst[orow * rows + ocol] = tile[x][y + j];
+            dst[orow * ldd + ocol] = tile[x][y + j];
     }
 }
 
@@ -350,14 +350,18 @@ optigpu_status tma_launch_facts(const DeviceInfo &dev, const TmaConfig &c, int &
 // Tile-rows per group of the TMA kernel's tile order.
 std::atomic<int> g_group_rows{16};
 
-bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, size_t esize)
+bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
+                  size_t esize)
 {
     if (esize != 2 && esize != 4)
         return false;
     const int64_t per16 = int64_t(16 / esize);
     if ((reinterpret_cast<uintptr_t>(src) & 15u) || (reinterpret_cast<uintptr_t>(dst) & 15u))
         return false;
-    if (rows <= 0 || cols <= 0 || rows % per16 || cols % per16)
+    if (rows <= 0 || cols <= 0 || rows % per16 || cols % per16 || lds % per16 || ldd % per16)
+        return false;
+    // Tensor-map strides are below 2^40 bytes.
+    if (lds > (int64_t(1) << 38) || ldd > (int64_t(1) << 38))
         return false;
     // TMA coordinates are int32 and global extents at most 2^32.
     if (rows > (int64_t(1) << 30) || cols > (int64_t(1) << 30))
@@ -365,8 +369,8 @@ bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, 
     return true;
 }
 
-optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols, size_t esize,
-                          cudaStream_t stream, int config)
+optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
+                          size_t esize, cudaStream_t stream, int config)
 {
     DeviceInfo dev;
     optigpu_status st = current_device(dev);
@@ -382,10 +386,10 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
     alignas(64) CUtensorMap ms, md;
     // Source: dim0 = cols (contiguous), dim1 = rows; box TC x TR.
     if ((st = encode_tensor_map_2d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
-                                   uint64_t(cols) * esize, uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
+                                   uint64_t(lds) * esize, uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
         return st;
     // Destination: dim0 = rows (contiguous), dim1 = cols; box TR x TC.
-    if ((st = encode_tensor_map_2d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(rows) * esize,
+    if ((st = encode_tensor_map_2d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(ldd) * esize,
                                    uint32_t(c.tr), uint32_t(c.tc))) != OPTIGPU_OK)
         return st;
     int ctas_per_sm = 1;
@@ -405,8 +409,8 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
                       "launch transpose tma");
 }
 
-optigpu_status launch_tile32(const void *src, void *dst, int64_t rows, int64_t cols, size_t esize,
-                             cudaStream_t stream)
+optigpu_status launch_tile32(const void *src, void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
+                             size_t esize, cudaStream_t stream)
 {
     const int64_t tiles_c = (cols + 31) / 32;
     const int64_t tiles = tiles_c * ((rows + 31) / 32);
@@ -415,14 +419,15 @@ optigpu_status launch_tile32(const void *src, void *dst, int64_t rows, int64_t c
     const dim3 block(32, 8);
     if (esize == 4)
         transpose_tile32_kernel<uint32_t><<<unsigned(tiles), block, 0, stream>>>(
-            static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), rows, cols, tiles_c);
+            static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), rows, cols, tiles_c, lds, ldd);
     else
         transpose_tile32_kernel<uint16_t><<<unsigned(tiles), block, 0, stream>>>(
-            static_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), rows, cols, tiles_c);
+            static_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), rows, cols, tiles_c, lds, ldd);
     return check_cuda(cudaGetLastError(), "launch transpose tile32");
 }
 
-optigpu_status validate(const void *src, const void *dst, int64_t rows, int64_t cols, int dtype)
+optigpu_status validate(const void *src, int64_t lds, const void *dst, int64_t ldd, int64_t rows, int64_t cols,
+                        int dtype)
 {
     if (!dtype_valid(dtype))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose: unknown dtype " + std::to_string(dtype));
@@ -430,16 +435,20 @@ optigpu_status validate(const void *src, const void *dst, int64_t rows, int64_t 
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: negative rows or cols");
     if (rows == 0 || cols == 0)
         return OPTIGPU_OK;
+    if (lds < cols || ldd < rows)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: leading dimensions must be lds >= cols and ldd >= rows");
     const size_t es = esize_of(optigpu_dtype(dtype));
-    if (rows > (int64_t(1) << 62) / cols || rows * cols > (int64_t(1) << 62) / int64_t(es))
-        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: rows * cols * element size too large");
+    const int64_t lim = (int64_t(1) << 62) / int64_t(es);
+    if (rows > lim / lds || cols > lim / ldd)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: matrix extent times element size too large");
     if (!src || !dst)
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: null pointer");
     if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) % es)
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: pointer not aligned to the element size");
-    const uintptr_t bytes = uintptr_t(rows * cols) * es;
+    // Byte spans actually touched: the first to the last element of each matrix.
+    const uintptr_t sb = uintptr_t((rows - 1) * lds + cols) * es, db = uintptr_t((cols - 1) * ldd + rows) * es;
     const uintptr_t a = reinterpret_cast<uintptr_t>(src), b = reinterpret_cast<uintptr_t>(dst);
-    if (a < b + bytes && b < a + bytes)
+    if (a < b + db && b < a + sb)
         return fail(OPTIGPU_ERR_OVERLAP, "transpose: src and dst overlap (the transpose is out-of-place)");
     return OPTIGPU_OK;
 }
@@ -474,16 +483,16 @@ optigpu_status transpose_launch_config(const void *src, void *dst, int64_t rows,
                                        int config, cudaStream_t stream)
 {
     if (config == int(tma_configs(esize).size()))
-        return launch_tile32(src, dst, rows, cols, esize, stream);
-    if (!tma_eligible(src, dst, rows, cols, esize))
+        return launch_tile32(src, dst, rows, cols, cols, rows, esize, stream);
+    if (!tma_eligible(src, dst, rows, cols, cols, rows, esize))
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: shape or alignment not eligible for TMA");
-    return launch_tma(src, dst, rows, cols, esize, stream, config);
+    return launch_tma(src, dst, rows, cols, cols, rows, esize, stream, config);
 }
 
-optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype,
-                                  int kernel, cudaStream_t stream)
+optigpu_status transpose_dispatch_pitched(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t rows,
+                                          int64_t cols, int dtype, int kernel, cudaStream_t stream)
 {
-    optigpu_status st = validate(src, dst, rows, cols, dtype);
+    optigpu_status st = validate(src, lds, dst, ldd, rows, cols, dtype);
     if (st != OPTIGPU_OK)
         return st;
     if (kernel < OPTIGPU_TRANSPOSE_AUTO || kernel > OPTIGPU_TRANSPOSE_TMA)
@@ -491,16 +500,30 @@ optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int6
     if (rows == 0 || cols == 0)
         return OPTIGPU_OK;
     const size_t es = esize_of(optigpu_dtype(dtype));
-    const bool tma_ok = tma_eligible(src, dst, rows, cols, es);
+    const bool tma_ok = tma_eligible(src, dst, rows, cols, lds, ldd, es);
     if (kernel == OPTIGPU_TRANSPOSE_TMA && !tma_ok)
         return fail(OPTIGPU_ERR_INVALID_ARG,
-                    "transpose: TMA kernel needs 16-byte aligned pointers and rows, cols multiples of 16/esize");
+                    "transpose: TMA kernel needs 16-byte aligned pointers and rows, cols, lds, ldd multiples of "
+                    "16/esize");
     const int choice = transpose_selected(es);
     if (kernel == OPTIGPU_TRANSPOSE_TMA)
-        return launch_tma(src, dst, rows, cols, es, stream, choice < int(tma_configs(es).size()) ? choice : 0);
+        return launch_tma(src, dst, rows, cols, lds, ldd, es, stream,
+                          choice < int(tma_configs(es).size()) ? choice : 0);
     if (kernel == OPTIGPU_TRANSPOSE_AUTO && tma_ok && choice < int(tma_configs(es).size()))
-        return launch_tma(src, dst, rows, cols, es, stream, choice);
-    return launch_tile32(src, dst, rows, cols, es, stream);
+        return launch_tma(src, dst, rows, cols, lds, ldd, es, stream, choice);
+    return launch_tile32(src, dst, rows, cols, lds, ldd, es, stream);
+}
+
+optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
+                                  cudaStream_t stream)
+{
+    return transpose_dispatch_pitched(src, cols, dst, rows, rows, cols, dtype, kernel, stream);
+}
+
+optigpu_status transpose_band_into(const void *band, void *dst, int64_t b, int64_t cols, int64_t ldd, int dtype,
+                                   cudaStream_t stream)
+{
+    return transpose_dispatch_pitched(band, cols, dst, ldd, b, cols, dtype, OPTIGPU_TRANSPOSE_AUTO, stream);
 }
 
 } // namespace optigpu
@@ -523,12 +546,19 @@ optigpu_status optigpu_transpose_ex(const void *src, void *dst, int64_t rows, in
     return transpose_dispatch(src, dst, rows, cols, int(dtype), int(kernel), static_cast<cudaStream_t>(stream));
 }
 
+optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t rows,
+                                         int64_t cols, optigpu_dtype dtype, optigpu_stream_t stream)
+{
+    return transpose_dispatch_pitched(src, lds, dst, ldd, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO,
+                                      static_cast<cudaStream_t>(stream));
+}
+
 int optigpu_transpose_tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols,
                                    optigpu_dtype dtype)
 {
     if (!dtype_valid(int(dtype)))
         return 0;
-    return tma_eligible(src, dst, rows, cols, esize_of(dtype)) ? 1 : 0;
+    return tma_eligible(src, dst, rows, cols, cols, rows, esize_of(dtype)) ? 1 : 0;
 }
 
 } // extern "C"

@@ -203,3 +203,11 @@ def test_host_entry_points_validate_on_the_host(lib):
     assert lib.optigpu_reduce_sum_host(FAKE, 5, N.FLOAT32, None, 0, None) == N.ERR_INVALID_ARG
     assert lib.optigpu_reduce_sum_host(FAKE + 2, 5, N.FLOAT32, FAKE, 0, None) == N.ERR_INVALID_ARG
     assert lib.optigpu_reduce_sum_host(FAKE, 5, N.FLOAT32, FAKE, 8, None) == N.ERR_INVALID_ARG
+
+
+def test_strided_transpose_validation(lib):
+    f = lib.optigpu_transpose_strided
+    assert f(FAKE, 3, FAKE + (1 << 20), 4, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG   # lds < cols
+    assert f(FAKE, 4, FAKE + (1 << 20), 3, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG   # ldd < rows
+    assert f(FAKE, 100, FAKE + 64, 4, 4, 4, N.FLOAT32, None) == N.ERR_OVERLAP           # src span reaches dst
+    assert f(None, 4, None, 4, 0, 4, N.FLOAT32, None) == N.OK

@@ -82,3 +82,20 @@ def test_back_to_back_host_calls_on_two_streams():
     torch.cuda.synchronize()
     assert o1.item() == api.reduce_sum(to_device(v1, "float32")).item()
     assert o2.item() == api.reduce_sum(to_device(v2, "float32")).item()
+
+
+@pytest.mark.parametrize("n,dtype", [((1 << 24) * 2 + 12345, "float32"), ((1 << 22) + 3, "int32")])
+def test_reduce_host_pageable_staged_path(n, dtype):
+    """Pageable input goes through the banded staging path; the result is the
+    same bits as the device call."""
+    a = workloads.vector(n, dtype, seed=77)
+    got = api.reduce_sum(host(a, dtype, pin=False)).item()
+    assert got == api.reduce_sum(to_device(a, dtype)).item()
+
+
+def test_transpose_host_pinned_and_pageable_agree():
+    a = workloads.matrix(4100, 2050, "float32", seed=9)
+    pinned = api.transpose(host(a, "float32", pin=True))
+    out = torch.empty((2050, 4100), dtype=torch.float32)
+    api.transpose(host(a, "float32", pin=False), out=out)
+    assert torch.equal(pinned.view(torch.int32), out.view(torch.int32))

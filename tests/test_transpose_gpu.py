@@ -167,3 +167,33 @@ def test_autotune_selects_a_valid_configuration():
     a = workloads.matrix(2048, 2048, "float32", seed=8)
     check(a, "float32", "auto")
     api.tune_select("transpose", torch.float32, 0)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("rows,cols,lds,ldd", [
+    (64, 64, 64, 64), (100, 37, 50, 120), (256, 128, 384, 264), (33, 65, 65, 33), (512, 512, 520, 776),
+])
+def test_strided_transpose_sub_blocks(dtype, rows, cols, lds, ldd):
+    """Pitched transpose: the source block is rows x cols inside a row pitch
+    lds, the destination block cols x rows inside a row pitch ldd; elements
+    outside the destination block keep their canary value."""
+    from paper_2605_13864_gb300 import _native as N
+    full = workloads.matrix(rows, lds, dtype, seed=rows * 3 + lds)
+    src = to_device(full, dtype)
+    tdt = src.dtype
+    canary = torch.full((cols, ldd), 0, dtype=torch.int16 if tdt in (torch.bfloat16, torch.float16)
+                        else torch.int32, device="cuda")
+    canary.fill_(0x3A3A)
+    dst = canary.view(tdt)
+    st = N.lib().optigpu_transpose_strided(src.data_ptr(), lds, dst.data_ptr(), ldd, rows, cols,
+                                           api.dtype_code(tdt), torch.cuda.current_stream().cuda_stream)
+    assert st == N.OK, N.lib().optigpu_last_error()
+    torch.cuda.synchronize()
+    got = to_host_bits(dst)
+    want = oracle.transpose(np.ascontiguousarray(full[:, :cols]))
+    want = want.view(np.uint32) if want.dtype == np.float32 else want
+    assert np.array_equal(got[:, :rows], want)
+    pad = got[:, rows:]
+    if pad.size:
+        assert (pad.view(np.uint16 if pad.dtype == np.uint16 else np.uint32) ==
+                (0x3A3A if pad.dtype == np.uint16 else 0x3A3A)).all()
