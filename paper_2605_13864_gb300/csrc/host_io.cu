@@ -128,31 +128,6 @@ optigpu_status join(HostIo &h, cudaStream_t user)
     return st;
 }
 
-// Device address of host memory [p, p + bytes) if it is page-locked and
-// mapped for the device (both ends checked), else nullptr.
-void *device_view_of_host(const void *p, size_t bytes)
-{
-    if (!p || bytes == 0)
-        return nullptr;
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
-        return nullptr;
-    const char *last = static_cast<const char *>(p) + bytes - 1;
-    cudaPointerAttributes b{};
-    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (b.type != cudaMemoryTypeHost ||
-        static_cast<char *>(b.devicePointer) != static_cast<char *>(a.devicePointer) + bytes - 1)
-        return nullptr;
-    return a.devicePointer;
-}
-
 bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
 {
     const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);

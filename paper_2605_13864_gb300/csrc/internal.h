@@ -53,6 +53,11 @@ uint64_t wait_limit_ns();
 // to zero (on `stream`), so counters kept in it start at 0.
 optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr);
 
+// Device address of host memory [p, p + bytes) when it is page-locked and
+// mapped for the device (checked at both ends of the range), else nullptr.
+// Kernels may then read and write it directly (over NVLink-C2C on GB300).
+void *device_view_of_host(const void *p, size_t bytes);
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point.
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,

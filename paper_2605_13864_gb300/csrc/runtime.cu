@@ -134,6 +134,29 @@ optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr)
     return OPTIGPU_OK;
 }
 
+void *device_view_of_host(const void *p, size_t bytes)
+{
+    if (!p || bytes == 0)
+        return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+        return nullptr;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    cudaPointerAttributes b{};
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<char *>(b.devicePointer) != static_cast<char *>(a.devicePointer) + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
                                     uint32_t box0, uint32_t box1)

@@ -12,6 +12,11 @@
 //      runs as ONE persistent batch kernel built from per-step tables (the
 //      kernel of batch.cu: same chunks, same results as the single calls),
 //      the outputs are copied back, and an event marks the step's end.
+//      Requests whose host buffers are pinned are copied by two copy kernels
+//      per step (a gather and a scatter through the device's mapping of the
+//      host memory, over NVLink-C2C on GB300) instead of one copy-engine call
+//      per buffer, so a step costs a fixed number of launches however many
+//      requests it holds; the data still lands in the device arena.
 // Requests that arrive while earlier steps run are admitted into the next
 // step on another stream, so their copies and kernels overlap on the device.
 //
@@ -45,6 +50,58 @@ double now_s()
 
 constexpr size_t kAlign = 256;
 size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// One contiguous copy of a step: host<->arena through the device's mapping
+// of pinned host memory, done by SMs instead of one copy-engine call each.
+struct CopyDesc {
+    const char *src;
+    char *dst;
+    int64_t bytes;
+    int64_t first_piece; // prefix of pieces over the step's copies
+};
+
+constexpr int64_t kPiece = 32768; // bytes per work piece
+
+// Copies every piece of `count` descriptors; CTAs stride over pieces.  Each
+// piece uses the widest unit (16, 4 or 1 bytes) that both addresses allow.
+__global__ void __launch_bounds__(256) copy_pieces_kernel(const CopyDesc *__restrict__ d, int32_t count,
+                                                          int64_t pieces)
+{
+    for (int64_t p = blockIdx.x; p < pieces; p += gridDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].first_piece <= p)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const CopyDesc c = d[lo];
+        const int64_t off = (p - c.first_piece) * kPiece;
+        const int64_t len = min(kPiece, c.bytes - off);
+        const char *src = c.src + off;
+        char *dst = c.dst + off;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
+        int64_t done = 0;
+        if ((al & 15u) == 0) {
+            const int64_t n = len / 16;
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+                d4[i] = s4[i];
+            done = n * 16;
+        } else if ((al & 3u) == 0) {
+            const int64_t n = len / 4;
+            const uint32_t *s1 = reinterpret_cast<const uint32_t *>(src);
+            uint32_t *d1 = reinterpret_cast<uint32_t *>(dst);
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+                d1[i] = s1[i];
+            done = n * 4;
+        }
+        for (int64_t i = done + threadIdx.x; i < len; i += blockDim.x)
+            dst[i] = src[i];
+    }
+}
 
 // Best-fit allocator over one device allocation; free ranges coalesce.
 struct Arena {
@@ -108,6 +165,8 @@ enum ReqState { QUEUED = 0, RUNNING = 1, DONE = 2 };
 
 struct Req {
     optigpu_request r{};
+    const char *zc_src = nullptr; // device views of pinned host buffers (or null)
+    char *zc_dst = nullptr;
     size_t in_bytes = 0, out_bytes = 0;
     size_t off_in = 0, off_out = 0;
     int state = QUEUED;
@@ -234,7 +293,7 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
     char *base = sv->arena.base;
     for (uint64_t tk : adm) {
         const Req &rq = sv->reqs[tk];
-        if (rq.in_bytes &&
+        if (rq.in_bytes && !rq.zc_dst &&
             (st = check_cuda(cudaMemcpyAsync(base + rq.off_in, rq.r.host_src, rq.in_bytes, cudaMemcpyHostToDevice, sc.s),
                              "server: copy in")) != OPTIGPU_OK)
             return st;
@@ -274,18 +333,59 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
         BatchTables t;
         if ((st = batch_tables(descs.data(), int32_t(descs.size()), batch_tile(config), t)) != OPTIGPU_OK)
             return st;
+        // Copy kernels' descriptors: gathers (host -> arena) then scatters.
+        std::vector<CopyDesc> copies;
+        int64_t gpieces = 0, spieces = 0;
+        for (uint64_t tk : adm) {
+            const Req &rq = sv->reqs[tk];
+            if (rq.zc_dst && rq.in_bytes) {
+                copies.push_back(CopyDesc{rq.zc_src, base + rq.off_in, int64_t(rq.in_bytes), gpieces});
+                gpieces += (int64_t(rq.in_bytes) + kPiece - 1) / kPiece;
+            }
+        }
+        const int32_t n_gather = int32_t(copies.size());
+        for (uint64_t tk : adm) {
+            const Req &rq = sv->reqs[tk];
+            if (rq.zc_dst && rq.out_bytes) {
+                copies.push_back(CopyDesc{base + rq.off_out, rq.zc_dst, int64_t(rq.out_bytes), spieces});
+                spieces += (int64_t(rq.out_bytes) + kPiece - 1) / kPiece;
+            }
+        }
+        const int32_t n_scatter = int32_t(copies.size()) - n_gather;
+        const BatchLayout L = batch_layout(int64_t(descs.size()), t.items, t.chunks);
+        const size_t table_bytes = L.off_part - L.off_inst;
+        const size_t off_copy = (L.total + 255) / 256 * 256;
+        const size_t copy_bytes = sizeof(CopyDesc) * copies.size();
+        if ((st = ensure_capacity(sc, off_copy + copy_bytes, table_bytes + copy_bytes)) != OPTIGPU_OK)
+            return st;
+        char *stage = static_cast<char *>(sc.h_stage);
+        char *ws = static_cast<char *>(sc.d_ws);
         if (t.items > 0) {
-            const BatchLayout L = batch_layout(int64_t(descs.size()), t.items, t.chunks);
-            const size_t table_bytes = L.off_part - L.off_inst;
-            if ((st = ensure_capacity(sc, L.total, table_bytes)) != OPTIGPU_OK)
-                return st;
-            char *stage = static_cast<char *>(sc.h_stage);
             std::memcpy(stage, t.insts.data(), sizeof(BatchInst) * t.insts.size());
             std::memcpy(stage + (L.off_items - L.off_inst), t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size());
-            char *ws = static_cast<char *>(sc.d_ws);
             if ((st = check_cuda(cudaMemcpyAsync(ws + L.off_inst, stage, table_bytes, cudaMemcpyHostToDevice, sc.s),
                                  "server: copy step tables")) != OPTIGPU_OK)
                 return st;
+        }
+        if (!copies.empty()) {
+            std::memcpy(stage + table_bytes, copies.data(), copy_bytes);
+            if ((st = check_cuda(cudaMemcpyAsync(ws + off_copy, stage + table_bytes, copy_bytes,
+                                                 cudaMemcpyHostToDevice, sc.s),
+                                 "server: copy step copy list")) != OPTIGPU_OK)
+                return st;
+        }
+        DeviceInfo dev;
+        if ((st = current_device(dev)) != OPTIGPU_OK)
+            return st;
+        const CopyDesc *d_copies = reinterpret_cast<const CopyDesc *>(ws + off_copy);
+        if (n_gather > 0) {
+            const int64_t grid = std::min<int64_t>(gpieces, int64_t(4) * dev.num_sms);
+            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies, n_gather, gpieces);
+            if ((st = check_cuda(cudaGetLastError(), "server: gather")) != OPTIGPU_OK)
+                return st;
+            ++sv->stats.launches;
+        }
+        if (t.items > 0) {
             if ((st = batch_launch(config, reinterpret_cast<BatchInst *>(ws + L.off_inst),
                                    reinterpret_cast<uint32_t *>(ws + L.off_items), t.items,
                                    reinterpret_cast<unsigned long long *>(ws + L.off_queue),
@@ -294,10 +394,17 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
                 return st;
             ++sv->stats.launches;
         }
+        if (n_scatter > 0) {
+            const int64_t grid = std::min<int64_t>(spieces, int64_t(4) * dev.num_sms);
+            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies + n_gather, n_scatter, spieces);
+            if ((st = check_cuda(cudaGetLastError(), "server: scatter")) != OPTIGPU_OK)
+                return st;
+            ++sv->stats.launches;
+        }
     }
     for (uint64_t tk : adm) {
         const Req &rq = sv->reqs[tk];
-        if (rq.out_bytes &&
+        if (rq.out_bytes && !rq.zc_dst &&
             (st = check_cuda(cudaMemcpyAsync(rq.r.host_dst, base + rq.off_out, rq.out_bytes, cudaMemcpyDeviceToHost,
                                              sc.s),
                              "server: copy out")) != OPTIGPU_OK)
@@ -370,6 +477,14 @@ optigpu_status submit_locked(optigpu_server *sv, const optigpu_request &r, int64
     rq.in_bytes = in_b;
     rq.out_bytes = out_b;
     rq.t_submit = now_s();
+    if (!(sv->flags & OPTIGPU_SERVER_PER_CALL)) {
+        // Pinned host buffers are copied by the step's copy kernels; others by
+        // the copy engines.
+        rq.zc_src = static_cast<const char *>(device_view_of_host(r.host_src, in_b));
+        rq.zc_dst = static_cast<char *>(device_view_of_host(r.host_dst, out_b));
+        if ((in_b && !rq.zc_src) || !rq.zc_dst)
+            rq.zc_src = nullptr, rq.zc_dst = nullptr;
+    }
     rq.trace_index = trace_index;
     sv->reqs.emplace(tk, rq);
     sv->pending.push_back(tk);

@@ -105,6 +105,20 @@ def test_served_results_equal_oracle_and_single_calls(per_call, compensated):
     sv.close()
 
 
+def test_pageable_and_pinned_requests_mixed():
+    """Pinned requests go through the step's copy kernels, pageable ones
+    through copy-engine calls; both give the oracle's results."""
+    inst, data = mixed(24, count=40)
+    sv = api.Server(budget_bytes=256 << 20, max_slots=64, n_streams=2)
+    reqs = [make_request(i, a, pin=(k % 2 == 0)) for k, (i, a) in enumerate(zip(inst, data))]
+    for op, s, d in reqs:
+        sv.submit(op, s, d)
+    sv.drain()
+    for i, a, (op, s, d) in zip(inst, data, reqs):
+        check(i, a, op, s, d)
+    sv.close()
+
+
 def test_budget_and_slots_bound_admission():
     I = workloads.Instance
     inst = [I(0, "float32", 256, 256) for _ in range(12)]  # 256 KiB in + 256 KiB out each
