@@ -331,7 +331,8 @@ optigpu_status optigpu_server_submit(optigpu_server *server, const optigpu_reque
                                      uint64_t *ticket);
 
 /* One round of the loop: completes finished steps, admits queued requests in
- * arrival order into every free stream while slots and budget allow, and
+ * arrival order into every free stream while slots and budget allow (one
+ * step takes at most max_slots / n_streams requests, so steps overlap), and
  * launches them.  *launched (may be NULL) = number of steps launched. */
 optigpu_status optigpu_server_step(optigpu_server *server, int32_t *launched);
 

@@ -431,8 +431,11 @@ optigpu_status step_locked(optigpu_server *sv, int32_t *launched)
             continue;
         if (sv->pending.empty())
             break;
+        // A step takes at most its share of the slots, so that several steps
+        // (on different streams) overlap when the queue is long.
+        const int32_t per_step = std::max<int32_t>(1, sv->max_slots / int32_t(sv->streams.size()));
         std::vector<uint64_t> adm;
-        while (!sv->pending.empty() && sv->running < sv->max_slots) {
+        while (!sv->pending.empty() && sv->running < sv->max_slots && int32_t(adm.size()) < per_step) {
             Req &rq = sv->reqs[sv->pending.front()];
             size_t a = 0, b = 0;
             if (!sv->arena.alloc(rq.in_bytes, a))
@@ -546,6 +549,11 @@ optigpu_status optigpu_server_create(size_t mem_budget_bytes, int32_t max_slots,
                 break;
             if ((st = check_cuda(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming), "server: event")) !=
                 OPTIGPU_OK)
+                break;
+            // Step tables up to ~8 MiB on the device and 4 MiB of pinned
+            // staging from the start: growing them later costs a device-wide
+            // synchronisation in the middle of serving.
+            if ((st = ensure_capacity(sc, size_t(4) << 20, size_t(2) << 20)) != OPTIGPU_OK)
                 break;
         }
     }
