@@ -32,11 +32,13 @@ namespace {
 
 constexpr int kBatchThreads = 256;
 
-template <int TILE>
+// Largest shared tile, in 32-bit words, for tiles of `AREA` elements: the row
+// pitch S is TW + 1 words (TW + 2 halves for 16-bit data), so TH * S is at
+// most 1.5 * AREA words (reached at TW = 2 for 4-byte elements).
+template <int AREA>
 struct BatchShared {
     union {
-        uint32_t t32[TILE][TILE + 1];
-        uint16_t t16[TILE][TILE + 2];
+        uint32_t tile[AREA + AREA / 2];
         ReduceCore<OPTIGPU_INT32, false>::Shared ri;
         ReduceCore<OPTIGPU_FLOAT32, false>::Shared rf;
         ReduceCore<OPTIGPU_FLOAT32, true>::Shared rfc;
@@ -50,30 +52,42 @@ struct BatchShared {
     int last;
 };
 
-// One TILE x TILE tile of a transpose: coalesced row reads into a padded
-// shared tile, coalesced row writes of its columns.  Edges are predicated.
-template <int TILE, typename T, typename Tile>
-__device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t local, Tile &tile)
+// Row pitch of the shared tile in elements.  Reading a tile column means
+// consecutive lanes step by one pitch; an odd pitch in 32-bit words puts them
+// in distinct banks (4-byte: TW + 1, or 1 for a one-column tile; 2-byte:
+// TW + 2 halves = an odd word count for TW >= 4, one word for TW <= 2).
+template <typename T>
+__device__ __forceinline__ int tile_pitch(int tw)
 {
-    constexpr int ROWS_PER_PASS = kBatchThreads / TILE;
+    if (sizeof(T) == 4)
+        return tw == 1 ? 1 : tw + 1;
+    return tw <= 2 ? 2 : tw + 2;
+}
+
+// One TH x TW tile of a transpose: coalesced reads of source rows into the
+// shared tile, coalesced writes of destination rows (= tile columns).  Edges
+// are predicated.
+template <typename T>
+__device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t local, T *tile)
+{
     const T *src = static_cast<const T *>(in.src);
     T *dst = static_cast<T *>(in.dst);
-    const int64_t tr = local / in.aux, tc = local - (local / in.aux) * in.aux;
-    const int64_t r0 = tr * TILE, c0 = tc * TILE;
-    const int x = threadIdx.x % TILE, y0 = threadIdx.x / TILE;
+    const int th_l = in.th_log2, tw_l = in.tw_log2;
+    const int th = 1 << th_l, tw = 1 << tw_l, area = th << tw_l;
+    const int S = tile_pitch<T>(tw);
+    const int64_t tr = local / in.aux, tc = local - tr * in.aux;
+    const int64_t r0 = tr << th_l, c0 = tc << tw_l;
     const int64_t rows = in.rows, cols = in.cols;
-#pragma unroll
-    for (int j = 0; j < TILE; j += ROWS_PER_PASS) {
-        const int64_t r = r0 + y0 + j, c = c0 + x;
-        if (r < rows && c < cols)
-            tile[y0 + j][x] = src[r * cols + c];
+    for (int e = threadIdx.x; e < area; e += kBatchThreads) {
+        const int r = e >> tw_l, c = e & (tw - 1);
+        if (r0 + r < rows && c0 + c < cols)
+            tile[r * S + c] = src[(r0 + r) * cols + c0 + c];
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < TILE; j += ROWS_PER_PASS) {
-        const int64_t orow = c0 + y0 + j, ocol = r0 + x;
-        if (orow < cols && ocol < rows)
-            dst[orow * rows + ocol] = tile[x][y0 + j];
+    for (int e = threadIdx.x; e < area; e += kBatchThreads) {
+        const int c = e >> th_l, r = e & (th - 1);
+        if (c0 + c < cols && r0 + r < rows)
+            dst[(c0 + c) * rows + r0 + r] = tile[r * S + c];
     }
 }
 
@@ -100,12 +114,12 @@ __device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local,
     }
 }
 
-template <int TILE>
+template <int AREA>
 __global__ void __launch_bounds__(kBatchThreads)
 batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ item_inst, int64_t total_items,
              unsigned long long *queue, unsigned *inst_done, void *partials, int compensated)
 {
-    __shared__ BatchShared<TILE> sh;
+    __shared__ BatchShared<AREA> sh;
     const int t = threadIdx.x;
     if (t == 0) {
         const int64_t it = int64_t(atomicAdd(queue, 1ull));
@@ -126,9 +140,9 @@ batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ i
         const int64_t local = item - in.first_item;
         if (in.op == OPTIGPU_OP_TRANSPOSE) {
             if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
-                transpose_tile<TILE, uint16_t>(in, local, sh.u.t16);
+                transpose_tile<uint16_t>(in, local, reinterpret_cast<uint16_t *>(sh.u.tile));
             else
-                transpose_tile<TILE, uint32_t>(in, local, sh.u.t32);
+                transpose_tile<uint32_t>(in, local, sh.u.tile);
         } else {
             switch (in.dtype * 2 + (compensated ? 1 : 0)) {
             case OPTIGPU_INT32 * 2:
@@ -165,7 +179,7 @@ batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ i
 }
 
 struct BatchConfig {
-    int tile;
+    int tile; // transpose tile area in elements
     int ctas_per_sm; // 0 = as many as fit
     const void *fn;
     const char *name;
@@ -174,10 +188,10 @@ struct BatchConfig {
 const std::vector<BatchConfig> &batch_configs()
 {
     static const std::vector<BatchConfig> c = {
-        {64, 0, reinterpret_cast<const void *>(&batch_kernel<64>), "batch tile64 ctas/SM=max"},
-        {64, 4, reinterpret_cast<const void *>(&batch_kernel<64>), "batch tile64 ctas/SM=4"},
-        {32, 0, reinterpret_cast<const void *>(&batch_kernel<32>), "batch tile32 ctas/SM=max"},
-        {32, 8, reinterpret_cast<const void *>(&batch_kernel<32>), "batch tile32 ctas/SM=8"},
+        {4096, 0, reinterpret_cast<const void *>(&batch_kernel<4096>), "batch tile area 4096 ctas/SM=max"},
+        {4096, 4, reinterpret_cast<const void *>(&batch_kernel<4096>), "batch tile area 4096 ctas/SM=4"},
+        {1024, 0, reinterpret_cast<const void *>(&batch_kernel<1024>), "batch tile area 1024 ctas/SM=max"},
+        {1024, 8, reinterpret_cast<const void *>(&batch_kernel<1024>), "batch tile area 1024 ctas/SM=8"},
     };
     return c;
 }
@@ -212,7 +226,31 @@ BatchLayout batch_layout(int64_t count, int64_t items, int64_t chunks)
     return L;
 }
 
-optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int tile, BatchTables &t)
+void batch_tile_shape(int64_t rows, int64_t cols, int area, int &th_log2, int &tw_log2)
+{
+    auto log2_ceil = [](int64_t v) {
+        int l = 0;
+        while ((int64_t(1) << l) < v)
+            ++l;
+        return l;
+    };
+    int a_l = log2_ceil(area);
+    const int side = a_l / 2;
+    const int pr = std::min(log2_ceil(std::max<int64_t>(rows, 1)), a_l);
+    const int pc = std::min(log2_ceil(std::max<int64_t>(cols, 1)), a_l);
+    if (pr >= side && pc >= side) {
+        th_log2 = side;
+        tw_log2 = a_l - side;
+    } else if (pc < side) {
+        tw_log2 = pc;
+        th_log2 = std::min(pr, a_l - pc);
+    } else {
+        th_log2 = pr;
+        tw_log2 = std::min(pc, a_l - pr);
+    }
+}
+
+optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, BatchTables &t)
 {
     t.insts.assign(size_t(count), BatchInst{});
     t.item_inst.clear();
@@ -232,8 +270,10 @@ optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int tile, 
             b.rows = d.rows;
             b.cols = d.cols;
             if (d.rows > 0 && d.cols > 0) {
-                const int64_t tc = (d.cols + tile - 1) / tile;
-                const int64_t trn = (d.rows + tile - 1) / tile;
+                batch_tile_shape(d.rows, d.cols, area, b.th_log2, b.tw_log2);
+                const int64_t th = int64_t(1) << b.th_log2, tw = int64_t(1) << b.tw_log2;
+                const int64_t tc = (d.cols + tw - 1) / tw;
+                const int64_t trn = (d.rows + th - 1) / th;
                 b.aux = tc;
                 n_items = tc * trn;
                 t.bytes += 2 * d.rows * d.cols * es;

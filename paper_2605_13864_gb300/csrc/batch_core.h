@@ -25,7 +25,15 @@ struct BatchInst {
     int32_t dtype;
     int32_t nitems;     // tiles or chunks
     int32_t vec_ok;     // sum: 16-byte aligned source
+    int32_t th_log2;    // transpose tile height (source rows) = 1 << th_log2
+    int32_t tw_log2;    // transpose tile width (source cols) = 1 << tw_log2
 };
+
+// Tile of a transpose instance: powers of two TH x TW with TH * TW <= area,
+// square (sqrt(area) on a side) when both sides allow, otherwise as wide as
+// the short side needs and as tall as the area allows, so skinny matrices
+// still move a full tile per work item.
+void batch_tile_shape(int64_t rows, int64_t cols, int area, int &th_log2, int &tw_log2);
 
 // Host image of one batch: instances, the item -> instance map and totals.
 struct BatchTables {
@@ -47,10 +55,11 @@ BatchLayout batch_layout(int64_t count, int64_t items, int64_t chunks);
 // Checks one descriptor like the single calls do.
 optigpu_status batch_validate(const optigpu_desc &d, int32_t index);
 
-// Fills `t` for `count` validated descriptors, transposes cut in tile x tile.
-optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int tile, BatchTables &t);
+// Fills `t` for `count` validated descriptors; transposes are cut into tiles
+// of at most `area` elements (batch_tile_shape).
+optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, BatchTables &t);
 
-// Transpose tile of batch configuration `config`.
+// Transpose tile area of batch configuration `config`.
 int batch_tile(int config);
 
 // Enqueues the queue reset and the persistent batch kernel on `stream`.
