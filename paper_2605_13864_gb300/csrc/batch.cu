@@ -64,12 +64,14 @@ __device__ __forceinline__ int tile_pitch(int tw)
     return tw <= 2 ? 2 : tw + 2;
 }
 
-// One TH x TW tile of a transpose: coalesced reads of source rows into the
-// shared tile, coalesced writes of destination rows (= tile columns).  Edges
-// are predicated.
-template <typename T>
+// One TH x TW tile (TH * TW <= AREA) of a transpose: coalesced reads of
+// source rows into the shared tile, coalesced writes of destination rows
+// (= tile columns).  Each thread first issues all of its AREA / 256 loads
+// into registers, so they are in flight together.  Edges are predicated.
+template <int AREA, typename T>
 __device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t local, T *tile)
 {
+    constexpr int PER = AREA / kBatchThreads;
     const T *src = static_cast<const T *>(in.src);
     T *dst = static_cast<T *>(in.dst);
     const int th_l = in.th_log2, tw_l = in.tw_log2;
@@ -78,15 +80,25 @@ __device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t loca
     const int64_t tr = local / in.aux, tc = local - tr * in.aux;
     const int64_t r0 = tr << th_l, c0 = tc << tw_l;
     const int64_t rows = in.rows, cols = in.cols;
-    for (int e = threadIdx.x; e < area; e += kBatchThreads) {
+    T v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * kBatchThreads;
         const int r = e >> tw_l, c = e & (tw - 1);
-        if (r0 + r < rows && c0 + c < cols)
-            tile[r * S + c] = src[(r0 + r) * cols + c0 + c];
+        v[k] = (e < area && r0 + r < rows && c0 + c < cols) ? src[(r0 + r) * cols + c0 + c] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * kBatchThreads;
+        if (e < area)
+            tile[(e >> tw_l) * S + (e & (tw - 1))] = v[k];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < area; e += kBatchThreads) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * kBatchThreads;
         const int c = e >> th_l, r = e & (th - 1);
-        if (c0 + c < cols && r0 + r < rows)
+        if (e < area && c0 + c < cols && r0 + r < rows)
             dst[(c0 + c) * rows + r0 + r] = tile[r * S + c];
     }
 }
@@ -140,9 +152,9 @@ batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ i
         const int64_t local = item - in.first_item;
         if (in.op == OPTIGPU_OP_TRANSPOSE) {
             if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
-                transpose_tile<uint16_t>(in, local, reinterpret_cast<uint16_t *>(sh.u.tile));
+                transpose_tile<AREA, uint16_t>(in, local, reinterpret_cast<uint16_t *>(sh.u.tile));
             else
-                transpose_tile<uint32_t>(in, local, sh.u.tile);
+                transpose_tile<AREA, uint32_t>(in, local, sh.u.tile);
         } else {
             switch (in.dtype * 2 + (compensated ? 1 : 0)) {
             case OPTIGPU_INT32 * 2:
