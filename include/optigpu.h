@@ -416,6 +416,13 @@ optigpu_status optigpu_tune_load(const char *path);
  * call).  OPTIGPU_OK otherwise. */
 optigpu_status optigpu_stream_status(optigpu_stream_t stream);
 
+/* Failure-detection self-test (the thesis has no counterpart): enqueues a
+ * kernel that waits, with the library's bounded device wait, on a barrier
+ * phase nothing completes.  After limit_ns (in (0, 10 s]) it gives up and
+ * records a timeout, so the next optigpu_stream_status on that stream returns
+ * OPTIGPU_ERR_TIMEOUT and the CUDA context stays usable.  No fault, no hang. */
+optigpu_status optigpu_selftest_wait_timeout(uint64_t limit_ns, optigpu_stream_t stream);
+
 /* Static description of a status code; never NULL. */
 const char *optigpu_status_string(optigpu_status status);
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "optigpu_tune_save": (_ci, [ctypes.c_char_p]),
     "optigpu_tune_load": (_ci, [ctypes.c_char_p]),
     "optigpu_stream_status": (_ci, [_vp]),
+    "optigpu_selftest_wait_timeout": (_ci, [_u64, _vp]),
     "optigpu_status_string": (ctypes.c_char_p, [_ci]),
     "optigpu_last_error": (ctypes.c_char_p, []),
     "optigpu_set_wait_limit_ns": (None, [_u64]),
