@@ -19,6 +19,15 @@ Definitions followed (thesis arxiv 2605.13864):
   ``sum |x|`` used to report errors.
 * ``sum_i64_chunked`` -- Listing 2.2 (Sec. 2.2.1): per-chunk partial sums,
   then a sequential sum of the partials.
+* ``transpose_strided`` / ``transpose_batched`` / ``transpose_inplace`` --
+  Listing 3.5 on pitched sub-blocks, on a batch of matrices, and in place
+  (swap a[i][j] with a[j][i] for i < j).
+* ``scan`` -- inclusive prefix sums (Sec. 9 future work): Listing 2.1's
+  loop keeping every intermediate sum, int64 for int32 input, double for
+  float input.
+* ``segmented_sums`` -- ``sum_i64`` / ``sum_f64`` per segment.
+* ``histogram_i32`` -- counts of int32 values in bins of an integer width
+  (Sec. 9 future work).
 
 Pins against things other than the oracle itself live in
 ``tests/test_oracle.py``.
@@ -77,6 +86,18 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = [vp, i64, ci]
             fn.restype = dbl
+        lib.oracle_transpose_strided.argtypes = [vp, i64, vp, i64, i64, i64, i64]
+        lib.oracle_transpose_strided.restype = None
+        lib.oracle_transpose_batched.argtypes = [vp, i64, vp, i64, i64, i64, i64, i64]
+        lib.oracle_transpose_batched.restype = None
+        lib.oracle_transpose_inplace.argtypes = [vp, i64, i64]
+        lib.oracle_transpose_inplace.restype = None
+        lib.oracle_scan_i32.argtypes = [vp, i64, vp]
+        lib.oracle_scan_i32.restype = None
+        lib.oracle_scan_f64.argtypes = [vp, i64, ci, vp]
+        lib.oracle_scan_f64.restype = None
+        lib.oracle_histogram_i32.argtypes = [vp, i64, i64, i64, i64, vp]
+        lib.oracle_histogram_i32.restype = None
         lib.oracle_decode_f16.argtypes = [ctypes.c_uint16]
         lib.oracle_decode_f16.restype = dbl
         lib.oracle_decode_bf16.argtypes = [ctypes.c_uint16]
@@ -187,3 +208,63 @@ def reduce_reference(a: np.ndarray, dtype: str | None = None) -> dict:
             "f64": sum_f64(a, kind),
             "f64_neumaier": sum_f64_neumaier(a, kind),
             "abs": sum_abs_f64(a, kind)}
+
+
+def transpose_strided(src: np.ndarray, lds: int, dst: np.ndarray, ldd: int, rows: int, cols: int) -> None:
+    """In place into ``dst`` (flat, pitch ``ldd``): dst[x*ldd + y] = src[y*lds + x]."""
+    src = _as_c(src)
+    if not dst.flags.c_contiguous:
+        raise ValueError("dst must be contiguous")
+    _load().oracle_transpose_strided(_ptr(src), lds, _ptr(dst), ldd, rows, cols, src.dtype.itemsize)
+
+
+def transpose_batched(src: np.ndarray) -> np.ndarray:
+    """(batch, rows, cols) -> (batch, cols, rows), each matrix transposed."""
+    src = _as_c(src)
+    b, r, c = src.shape
+    dst = np.empty((b, c, r), dtype=src.dtype)
+    _load().oracle_transpose_batched(_ptr(src), r * c, _ptr(dst), r * c, b, r, c, src.dtype.itemsize)
+    return dst
+
+
+def transpose_inplace(a: np.ndarray) -> np.ndarray:
+    """Transposes the square array ``a`` in place (and returns it)."""
+    if a.ndim != 2 or a.shape[0] != a.shape[1] or not a.flags.c_contiguous:
+        raise ValueError("transpose_inplace expects a contiguous square array")
+    _load().oracle_transpose_inplace(_ptr(a), a.shape[0], a.dtype.itemsize)
+    return a
+
+
+def scan(a: np.ndarray, dtype: str | None = None) -> np.ndarray:
+    """Inclusive prefix sums: int64 for int32 input, float64 for float input."""
+    kind = kind_of(a, dtype)
+    a = _as_c(a).reshape(-1)
+    if kind == "int32":
+        out = np.empty(a.size, dtype=np.int64)
+        _load().oracle_scan_i32(_ptr(a), a.size, _ptr(out))
+    else:
+        out = np.empty(a.size, dtype=np.float64)
+        _load().oracle_scan_f64(_ptr(a), a.size, _KIND[kind], _ptr(out))
+    return out
+
+
+def segmented_sums(a: np.ndarray, offsets, dtype: str | None = None) -> list:
+    """Sum of every segment a[offsets[s]:offsets[s+1]] (ints exact, floats in
+    double), each by the same sequential loop as sum_i64 / sum_f64."""
+    kind = kind_of(a, dtype)
+    a = _as_c(a).reshape(-1)
+    out = []
+    for s in range(len(offsets) - 1):
+        seg = a[offsets[s]:offsets[s + 1]]
+        out.append(sum_i64(seg) if kind == "int32" else sum_f64(seg, kind))
+    return out
+
+
+def histogram_i32(a: np.ndarray, lo: int, width: int, nbins: int) -> np.ndarray:
+    """counts[b] = #{x : lo + b*width <= x < lo + (b+1)*width}, as int64."""
+    a = _as_c(a).reshape(-1)
+    if a.dtype != np.int32:
+        raise TypeError("histogram_i32 expects int32")
+    counts = np.empty(nbins, dtype=np.int64)
+    _load().oracle_histogram_i32(_ptr(a), a.size, lo, width, nbins, _ptr(counts))
+    return counts

@@ -213,3 +213,88 @@ int64_t oracle_sum_i32_chunked(const int32_t *arr, int64_t n, int64_t chunk)
     }
     return sum;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Neighbouring problems (the thesis's Sec. 9 future work and the pitched /  */
+/* batched / in-place variants of Listing 3.5).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Listing 3.5 on sub-blocks of larger row-major arrays: out[x][y] = in[y][x]
+ * with the input row pitch lds and the output row pitch ldd (elements). */
+void oracle_transpose_strided(const void *src, int64_t lds, void *dst, int64_t ldd,
+                              int64_t rows, int64_t cols, int64_t esize)
+{
+    const unsigned char *in = (const unsigned char *)src;
+    unsigned char *out = (unsigned char *)dst;
+    for (int64_t x = 0; x < cols; x++)
+        for (int64_t y = 0; y < rows; y++)
+            memcpy(out + (x * ldd + y) * esize, in + (y * lds + x) * esize, (size_t)esize);
+}
+
+/* Listing 3.5 applied to `batch` dense matrices laid out stride_src (input)
+ * and stride_dst (output) elements apart. */
+void oracle_transpose_batched(const void *src, int64_t stride_src, void *dst, int64_t stride_dst,
+                              int64_t batch, int64_t rows, int64_t cols, int64_t esize)
+{
+    for (int64_t b = 0; b < batch; b++)
+        oracle_transpose((const unsigned char *)src + b * stride_src * esize,
+                         (unsigned char *)dst + b * stride_dst * esize, rows, cols, esize);
+}
+
+/* In-place transpose of an n x n matrix: swap a[i][j] and a[j][i] for every
+ * i < j (the diagonal stays). */
+void oracle_transpose_inplace(void *a, int64_t n, int64_t esize)
+{
+    unsigned char *m = (unsigned char *)a;
+    unsigned char t[8];
+    if (esize > 8)
+        return;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            unsigned char *p = m + (i * n + j) * esize, *q = m + (j * n + i) * esize;
+            memcpy(t, p, (size_t)esize);
+            memcpy(p, q, (size_t)esize);
+            memcpy(q, t, (size_t)esize);
+        }
+}
+
+/* Inclusive prefix sums, Listing 2.1's loop keeping every intermediate sum:
+ * out[i] = A(0) + ... + A(i).  int32 input: exact int64. */
+void oracle_scan_i32(const int32_t *arr, int64_t n, int64_t *out)
+{
+    int64_t sum = 0;
+    for (int64_t i = 0; i < n; i++) {
+        sum += (int64_t)arr[i];
+        out[i] = sum;
+    }
+}
+
+/* Float input: sequential double prefix sums of the exactly widened values. */
+void oracle_scan_f64(const void *arr, int64_t n, int dtype, double *out)
+{
+    double sum = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        sum += element_as_double(arr, i, dtype);
+        out[i] = sum;
+    }
+}
+
+/* Histogram of int32 values: bins of `width` >= 1 integers starting at lo;
+ * counts[b] = #{ i : lo + b*width <= x_i < lo + (b+1)*width }, b < nbins.
+ * Values outside [lo, lo + nbins*width) are not counted. */
+void oracle_histogram_i32(const int32_t *arr, int64_t n, int64_t lo, int64_t width,
+                          int64_t nbins, int64_t *counts)
+{
+    for (int64_t b = 0; b < nbins; b++)
+        counts[b] = 0;
+    if (width <= 0)
+        return;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t d = (int64_t)arr[i] - lo;
+        if (d < 0)
+            continue;
+        int64_t b = d / width;
+        if (b < nbins)
+            counts[b] += 1;
+    }
+}
