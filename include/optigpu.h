@@ -120,6 +120,17 @@ optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst
                                          int64_t rows, int64_t cols, optigpu_dtype dtype,
                                          optigpu_stream_t stream);
 
+/* A stack of equal transposes: for b < batch,
+ *   dst[b * stride_dst + c * rows + r] = src[b * stride_src + r * cols + c].
+ * Each matrix is dense; strides (elements) must be >= rows * cols.  One
+ * launch: the TMA kernel with 3-D tensor maps (the batch index is the third
+ * coordinate) when pointers, shapes and strides allow, else the padded tile
+ * kernel.  Errors as optigpu_transpose (OVERLAP on the touched byte spans). */
+optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, void *dst,
+                                         int64_t stride_dst, int64_t batch, int64_t rows,
+                                         int64_t cols, optigpu_dtype dtype,
+                                         optigpu_stream_t stream);
+
 /* 1 if the TMA kernel accepts this shape and these pointers, else 0. */
 int optigpu_transpose_tma_eligible(const void *src, const void *dst,
                                    int64_t rows, int64_t cols,

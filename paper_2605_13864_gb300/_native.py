@@ -46,6 +46,7 @@ SIGNATURES = {
     "optigpu_transpose_ex": (_ci, [_vp, _vp, _i64, _i64, _ci, _ci, _vp]),
     "optigpu_transpose_tma_eligible": (_ci, [_vp, _vp, _i64, _i64, _ci]),
     "optigpu_transpose_strided": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _ci, _vp]),
+    "optigpu_transpose_batched": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _i64, _ci, _vp]),
     "optigpu_reduce_sum": (_ci, [_vp, _i64, _ci, _vp, _vp]),
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),

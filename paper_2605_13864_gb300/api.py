@@ -62,6 +62,25 @@ def transpose(src: torch.Tensor, out: torch.Tensor | None = None, kernel: str = 
     return out
 
 
+def transpose_batched(src: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """(batch, rows, cols) CUDA tensor -> (batch, cols, rows): each matrix
+    transposed, in one launch."""
+    if src.dim() != 3 or not src.is_cuda:
+        raise ValueError("transpose_batched expects a 3-D CUDA tensor")
+    b, rows, cols = src.shape
+    if src.stride(2) != 1 or src.stride(1) != cols:
+        raise ValueError("each source matrix must be dense row-major")
+    if out is None:
+        out = torch.empty((b, cols, rows), dtype=src.dtype, device=src.device)
+    elif tuple(out.shape) != (b, cols, rows) or out.stride(2) != 1 or out.stride(1) != rows:
+        raise ValueError("out must be (batch, cols, rows) with dense matrices")
+    st = N.lib().optigpu_transpose_batched(src.data_ptr(), src.stride(0) if b > 1 else rows * cols,
+                                           out.data_ptr(), out.stride(0) if b > 1 else rows * cols,
+                                           b, rows, cols, dtype_code(src.dtype), _stream_ptr(stream))
+    N.check(st, "optigpu_transpose_batched")
+    return out
+
+
 def reduce_sum(x: torch.Tensor, compensated: bool = False, out: torch.Tensor | None = None,
                stream=None) -> torch.Tensor:
     """Sum of all elements (thesis Listing 2.1: reduce_sum(N, A)).

@@ -62,6 +62,10 @@ void *device_view_of_host(const void *p, size_t bytes);
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
                                     uint32_t box0, uint32_t box1);
+// Same with a third dimension (dim2, stride2_bytes) and a box depth of 1.
+optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDataType type,
+                                    uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
+                                    uint64_t stride2_bytes, uint32_t box0, uint32_t box1);
 
 // Transpose configurations: indices 0 .. n-2 are TMA kernels, n-1 is tile32.
 int transpose_num_configs(size_t esize);

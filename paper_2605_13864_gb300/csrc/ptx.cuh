@@ -112,6 +112,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst_smem, const CUtensorMap
                  : "memory");
 }
 
+// 3-D tiled TMA load (c2 = the batch index of a stack of matrices).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst_smem, const CUtensorMap *map, int32_t c0, int32_t c1,
+                                            int32_t c2, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst_smem),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+                 : "memory");
+}
+
+// 3-D tiled TMA store.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int32_t c0, int32_t c1, int32_t c2,
+                                             uint32_t src_smem)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group"
+                 " [%0, {%1, %2, %3}], [%4];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(src_smem)
+                 : "memory");
+}
+
 // 2-D tiled TMA store shared -> global; out-of-range parts of the box are
 // not written.  Tracked by the calling thread's bulk async-groups.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int32_t c0, int32_t c1,

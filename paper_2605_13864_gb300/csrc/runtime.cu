@@ -157,6 +157,45 @@ void *device_view_of_host(const void *p, size_t bytes)
     return a.devicePointer;
 }
 
+namespace {
+optigpu_status encode_entry();
+} // namespace
+
+optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDataType type,
+                                    uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
+                                    uint64_t stride2_bytes, uint32_t box0, uint32_t box1)
+{
+    optigpu_status st = encode_entry();
+    if (st != OPTIGPU_OK)
+        return st;
+    const cuuint64_t dims[3] = {dim0, dim1, dim2};
+    const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
+    const cuuint32_t box[3] = {box0, box1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(OPTIGPU_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed with CUresult " + std::to_string(int(r)));
+    return OPTIGPU_OK;
+}
+
+namespace {
+optigpu_status encode_entry()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(OPTIGPU_ERR_CUDA, "cuTensorMapEncodeTiled entry point not available");
+        g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    return OPTIGPU_OK;
+}
+} // namespace
+
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
                                     uint32_t box0, uint32_t box1)

@@ -46,13 +46,17 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256)
 transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t rows,
-                        int64_t cols, int64_t tiles_c, int64_t lds, int64_t ldd)
+                        int64_t cols, int64_t tiles_c, int64_t lds, int64_t ldd,
+                        int64_t tiles_per_mat, int64_t bs, int64_t bd)
 {
     // 4-byte rows are padded by one element, 2-byte rows by two, so that a
     // column of the tile spans 32 distinct 4-byte banks.
     constexpr int PAD = sizeof(T) == 4 ? 1 : 2;
     __shared__ T tile[32][32 + PAD];
-    const int64_t id = blockIdx.x;
+    const int64_t b = int64_t(blockIdx.x) / tiles_per_mat;
+    const int64_t id = int64_t(blockIdx.x) - b * tiles_per_mat;
+    src += b * bs;
+    dst += b * bd;
     const int64_t tr = id / tiles_c;
     const int64_t tc = id - tr * tiles_c;
     const int64_t r0 = tr * 32, c0 = tc * 32;
@@ -137,8 +141,11 @@ struct TmaTile {
 // group x TR elements, instead of one short piece per destination row.
 struct TileOrder {
     int32_t tiles_r, tiles_c, group;
-    __device__ __forceinline__ void coords(int64_t id, int32_t &tr, int32_t &tc) const
+    int64_t tiles_per_mat; // tiles_r * tiles_c; ids run matrix by matrix
+    __device__ __forceinline__ void coords(int64_t id, int32_t &tr, int32_t &tc, int32_t &b) const
     {
+        b = int32_t(id / tiles_per_mat);
+        id -= int64_t(b) * tiles_per_mat;
         const int64_t per_group = int64_t(group) * tiles_c;
         const int32_t g = int32_t(id / per_group);
         const int32_t within = int32_t(id - int64_t(g) * per_group);
@@ -154,7 +161,9 @@ struct TileOrder {
 // load has landed (transaction bytes), empty[s] when every consumer warp has
 // taken its micro-blocks out.  NOB output buffers let up to NOB - 1 tile
 // stores still read shared memory while the next tile is written.
-template <int ESIZE, int TR, int TC, int STAGES, int NOB>
+// RANK 2: one matrix; RANK 3: a stack of matrices, the batch index being
+// the tensor maps' third coordinate.
+template <int ESIZE, int TR, int TC, int STAGES, int NOB, int RANK = 2>
 __global__ void __launch_bounds__(TmaTile<ESIZE, TR, TC>::THREADS + 32, 1)
 transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
                      const __grid_constant__ CUtensorMap tm_dst, TileOrder order,
@@ -197,10 +206,13 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
                 atomicOr(status, DEV_ERR_WAIT_TIMEOUT);
                 break;
             }
-            int32_t tr, tc;
-            order.coords(first + k * stride, tr, tc);
+            int32_t tr, tc, b;
+            order.coords(first + k * stride, tr, tc, b);
             ptx::mbar_arrive_expect_tx(full_bar + 8u * s, Tile::BYTES);
-            ptx::tma_load_2d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, full_bar + 8u * s);
+            if (RANK == 3)
+                ptx::tma_load_3d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, b, full_bar + 8u * s);
+            else
+                ptx::tma_load_2d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, full_bar + 8u * s);
         }
         // Before leaving, let every load still in flight land (bounded), so no
         // copy targets this CTA's shared memory after the consumers are gone.
@@ -256,9 +268,12 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
         ptx::fence_proxy_async_smem();
         ptx::named_bar_sync(2, NCONS);
         if (t == 0) {
-            int32_t tr, tc;
-            order.coords(first + k * stride, tr, tc);
-            ptx::tma_store_2d(&tm_dst, tr * TR, tc * TC, obuf);
+            int32_t tr, tc, b;
+            order.coords(first + k * stride, tr, tc, b);
+            if (RANK == 3)
+                ptx::tma_store_3d(&tm_dst, tr * TR, tc * TC, b, obuf);
+            else
+                ptx::tma_store_2d(&tm_dst, tr * TR, tc * TC, obuf);
             ptx::bulk_commit_group();
         }
     }
@@ -272,7 +287,8 @@ struct TmaConfig {
     int esize;
     int tr, tc, stages, nob, threads;
     uint32_t tile_bytes;
-    const void *fn;
+    const void *fn;  // one matrix (2-D tensor maps)
+    const void *fn3; // a stack of matrices (3-D tensor maps)
     const char *name;
 };
 
@@ -281,7 +297,8 @@ TmaConfig make_config(const char *name)
 {
     using Tile = TmaTile<ESIZE, TR, TC>;
     return TmaConfig{ESIZE, TR, TC, STAGES, NOB, Tile::THREADS + 32, Tile::BYTES,
-                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB>), name};
+                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 2>),
+                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 3>), name};
 }
 
 // The compiled TMA configurations per element size; index 0 is the default.
@@ -322,21 +339,21 @@ struct LaunchFacts {
 std::mutex g_facts_mu;
 std::map<std::pair<int, const void *>, LaunchFacts> g_facts;
 
-optigpu_status tma_launch_facts(const DeviceInfo &dev, const TmaConfig &c, int &ctas_per_sm)
+optigpu_status tma_launch_facts(const DeviceInfo &dev, const TmaConfig &c, const void *fn, int &ctas_per_sm)
 {
     std::lock_guard<std::mutex> lk(g_facts_mu);
-    LaunchFacts &f = g_facts[{dev.device, c.fn}];
+    LaunchFacts &f = g_facts[{dev.device, fn}];
     if (!f.ready) {
         const size_t smem = tma_smem_bytes(c);
         if (smem > dev.max_smem_optin)
             return fail(OPTIGPU_ERR_INVALID_ARG, std::string("transpose config needs too much shared memory: ") + c.name);
         optigpu_status st = check_cuda(
-            cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
             "cudaFuncSetAttribute(transpose tma smem)");
         if (st != OPTIGPU_OK)
             return st;
         int n = 0;
-        st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, c.fn, c.threads, smem),
+        st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, c.threads, smem),
                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(transpose tma)");
         if (st != OPTIGPU_OK)
             return st;
@@ -369,8 +386,14 @@ bool tma_eligible(const void *src, const void *dst, int64_t rows, int64_t cols, 
     return true;
 }
 
+// A stack of `batch` matrices: matrix b of src starts bs elements after
+// matrix b-1 (dst: bd).  batch == 1 is the single-matrix case.
+struct Stack {
+    int64_t batch = 1, bs = 0, bd = 0;
+};
+
 optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
-                          size_t esize, cudaStream_t stream, int config)
+                          size_t esize, cudaStream_t stream, int config, Stack stack = Stack())
 {
     DeviceInfo dev;
     optigpu_status st = current_device(dev);
@@ -382,47 +405,65 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
     if (config < 0 || config >= int(configs.size()))
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: unknown TMA configuration");
     const TmaConfig &c = configs[size_t(config)];
+    const bool rank3 = stack.batch > 1;
     const CUtensorMapDataType type = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     alignas(64) CUtensorMap ms, md;
-    // Source: dim0 = cols (contiguous), dim1 = rows; box TC x TR.
-    if ((st = encode_tensor_map_2d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
-                                   uint64_t(lds) * esize, uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
-        return st;
-    // Destination: dim0 = rows (contiguous), dim1 = cols; box TR x TC.
-    if ((st = encode_tensor_map_2d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(ldd) * esize,
-                                   uint32_t(c.tr), uint32_t(c.tc))) != OPTIGPU_OK)
-        return st;
+    if (!rank3) {
+        // Source: dim0 = cols (contiguous), dim1 = rows; box TC x TR.
+        if ((st = encode_tensor_map_2d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
+                                       uint64_t(lds) * esize, uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
+            return st;
+        // Destination: dim0 = rows (contiguous), dim1 = cols; box TR x TC.
+        if ((st = encode_tensor_map_2d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(ldd) * esize,
+                                       uint32_t(c.tr), uint32_t(c.tc))) != OPTIGPU_OK)
+            return st;
+    } else {
+        // dim2 = the matrix index, strides bs / bd elements.
+        if ((st = encode_tensor_map_3d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
+                                       uint64_t(stack.batch), uint64_t(lds) * esize, uint64_t(stack.bs) * esize,
+                                       uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
+            return st;
+        if ((st = encode_tensor_map_3d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(stack.batch),
+                                       uint64_t(ldd) * esize, uint64_t(stack.bd) * esize, uint32_t(c.tr),
+                                       uint32_t(c.tc))) != OPTIGPU_OK)
+            return st;
+    }
+    const void *fn = rank3 ? c.fn3 : c.fn;
     int ctas_per_sm = 1;
-    if ((st = tma_launch_facts(dev, c, ctas_per_sm)) != OPTIGPU_OK)
+    if ((st = tma_launch_facts(dev, c, fn, ctas_per_sm)) != OPTIGPU_OK)
         return st;
     const int64_t tiles_c = (cols + c.tc - 1) / c.tc;
     const int64_t tiles_r = (rows + c.tr - 1) / c.tr;
-    const int64_t num_tiles = tiles_r * tiles_c;
+    const int64_t per_mat = tiles_r * tiles_c;
+    const int64_t num_tiles = per_mat * stack.batch;
     const int64_t grid = std::min<int64_t>(num_tiles, int64_t(ctas_per_sm) * dev.num_sms);
     const size_t smem = tma_smem_bytes(c);
     const uint64_t limit = wait_limit_ns();
-    TileOrder order{int32_t(tiles_r), int32_t(tiles_c),
-                    std::max(1, std::min(g_group_rows.load(), int(tiles_r)))};
+    TileOrder order{int32_t(tiles_r), int32_t(tiles_c), std::max(1, std::min(g_group_rows.load(), int(tiles_r))),
+                    per_mat};
     void *args[] = {&ms, &md, &order, const_cast<int64_t *>(&num_tiles), const_cast<uint64_t *>(&limit),
                     &dev.status_word};
-    return check_cuda(cudaLaunchKernel(c.fn, dim3(unsigned(grid)), dim3(unsigned(c.threads)), args, smem, stream),
+    return check_cuda(cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(unsigned(c.threads)), args, smem, stream),
                       "launch transpose tma");
 }
 
 optigpu_status launch_tile32(const void *src, void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
-                             size_t esize, cudaStream_t stream)
+                             size_t esize, cudaStream_t stream, Stack stack = Stack())
 {
     const int64_t tiles_c = (cols + 31) / 32;
-    const int64_t tiles = tiles_c * ((rows + 31) / 32);
-    if (tiles > int64_t(0x7fffffff))
+    const int64_t per_mat = tiles_c * ((rows + 31) / 32);
+    if (per_mat > int64_t(0x7fffffff) / stack.batch)
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: too many 32x32 tiles for one launch");
+    const int64_t tiles = per_mat * stack.batch;
     const dim3 block(32, 8);
     if (esize == 4)
         transpose_tile32_kernel<uint32_t><<<unsigned(tiles), block, 0, stream>>>(
-            static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), rows, cols, tiles_c, lds, ldd);
+            static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst), rows, cols, tiles_c, lds, ldd, per_mat,
+            stack.bs, stack.bd);
     else
         transpose_tile32_kernel<uint16_t><<<unsigned(tiles), block, 0, stream>>>(
-            static_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), rows, cols, tiles_c, lds, ldd);
+            static_cast<const uint16_t *>(src), static_cast<uint16_t *>(dst), rows, cols, tiles_c, lds, ldd, per_mat,
+            stack.bs, stack.bd);
     return check_cuda(cudaGetLastError(), "launch transpose tile32");
 }
 
@@ -520,6 +561,47 @@ optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int6
     return transpose_dispatch_pitched(src, cols, dst, rows, rows, cols, dtype, kernel, stream);
 }
 
+// `batch` dense rows x cols matrices, stride_src / stride_dst elements apart.
+optigpu_status transpose_batched_dispatch(const void *src, int64_t stride_src, void *dst, int64_t stride_dst,
+                                          int64_t batch, int64_t rows, int64_t cols, int dtype, cudaStream_t stream)
+{
+    if (!dtype_valid(dtype))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_batched: unknown dtype " + std::to_string(dtype));
+    if (batch < 0 || rows < 0 || cols < 0)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: negative size");
+    if (batch == 0 || rows == 0 || cols == 0)
+        return OPTIGPU_OK;
+    if (batch == 1)
+        return transpose_dispatch(src, dst, rows, cols, dtype, OPTIGPU_TRANSPOSE_AUTO, stream);
+    const size_t es = esize_of(optigpu_dtype(dtype));
+    const int64_t lim = (int64_t(1) << 62) / int64_t(es);
+    if (rows > lim / cols || batch > (int64_t(1) << 31))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: sizes too large");
+    const int64_t n = rows * cols;
+    if (stride_src < n || stride_dst < n)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: strides must be >= rows * cols");
+    if (stride_src > lim / batch || stride_dst > lim / batch)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: strides too large");
+    if (!src || !dst)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: null pointer");
+    if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) % es)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_batched: pointer not aligned to the element size");
+    const uintptr_t sb = uintptr_t((batch - 1) * stride_src + n) * es, db = uintptr_t((batch - 1) * stride_dst + n) * es;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src), b = reinterpret_cast<uintptr_t>(dst);
+    if (a < b + db && b < a + sb)
+        return fail(OPTIGPU_ERR_OVERLAP, "transpose_batched: src and dst overlap");
+    Stack stack;
+    stack.batch = batch;
+    stack.bs = stride_src;
+    stack.bd = stride_dst;
+    const int64_t per16 = int64_t(16 / es);
+    const int choice = transpose_selected(es);
+    if (tma_eligible(src, dst, rows, cols, cols, rows, es) && stride_src % per16 == 0 && stride_dst % per16 == 0 &&
+        choice < int(tma_configs(es).size()))
+        return launch_tma(src, dst, rows, cols, cols, rows, es, stream, choice, stack);
+    return launch_tile32(src, dst, rows, cols, cols, rows, es, stream, stack);
+}
+
 optigpu_status transpose_band_into(const void *band, void *dst, int64_t b, int64_t cols, int64_t ldd, int dtype,
                                    cudaStream_t stream)
 {
@@ -550,6 +632,14 @@ optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst
                                          int64_t cols, optigpu_dtype dtype, optigpu_stream_t stream)
 {
     return transpose_dispatch_pitched(src, lds, dst, ldd, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO,
+                                      static_cast<cudaStream_t>(stream));
+}
+
+optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, void *dst, int64_t stride_dst,
+                                         int64_t batch, int64_t rows, int64_t cols, optigpu_dtype dtype,
+                                         optigpu_stream_t stream)
+{
+    return transpose_batched_dispatch(src, stride_src, dst, stride_dst, batch, rows, cols, int(dtype),
                                       static_cast<cudaStream_t>(stream));
 }
 

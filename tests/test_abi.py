@@ -211,3 +211,12 @@ def test_strided_transpose_validation(lib):
     assert f(FAKE, 4, FAKE + (1 << 20), 3, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG   # ldd < rows
     assert f(FAKE, 100, FAKE + 64, 4, 4, 4, N.FLOAT32, None) == N.ERR_OVERLAP           # src span reaches dst
     assert f(None, 4, None, 4, 0, 4, N.FLOAT32, None) == N.OK
+
+
+def test_batched_transpose_validation(lib):
+    f = lib.optigpu_transpose_batched
+    assert f(FAKE, 15, FAKE + (1 << 30), 16, 2, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG   # stride < n
+    assert f(FAKE, 16, FAKE + 64, 16, 2, 4, 4, N.FLOAT32, None) == N.ERR_OVERLAP
+    assert f(FAKE, 16, FAKE + (1 << 30), 16, -1, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert f(None, 16, None, 16, 0, 4, 4, N.FLOAT32, None) == N.OK
+    assert f(FAKE, 16, FAKE + (1 << 30), 16, 2, 4, 4, 12, None) == N.ERR_UNSUPPORTED_DTYPE
