@@ -131,6 +131,12 @@ optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, vo
                                          int64_t cols, optigpu_dtype dtype,
                                          optigpu_stream_t stream);
 
+/* In-place transpose of the square n x n matrix `a` (dense row-major):
+ * a[j][i] <- a[i][j] for all i, j.  Each CTA swaps one pair of 64 x 64 tiles
+ * through shared memory.  n in [0, 2^30]; errors as optigpu_transpose. */
+optigpu_status optigpu_transpose_inplace(void *a, int64_t n, optigpu_dtype dtype,
+                                         optigpu_stream_t stream);
+
 /* 1 if the TMA kernel accepts this shape and these pointers, else 0. */
 int optigpu_transpose_tma_eligible(const void *src, const void *dst,
                                    int64_t rows, int64_t cols,
@@ -170,6 +176,18 @@ optigpu_status optigpu_reduce_sum(const void *src, int64_t n,
 optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
                                      optigpu_dtype dtype, void *out,
                                      uint32_t flags, optigpu_stream_t stream);
+
+/* Segmented sums: out[s] = sum of src[offsets[s] .. offsets[s+1]) for
+ * s < nseg, each bit-identical to optigpu_reduce_sum_ex on that segment.
+ *   offsets  HOST array of nseg + 1 non-decreasing element offsets (< 2^40).
+ *   out      device array of nseg 8-byte results (int64 / double); empty
+ *            segments give 0.
+ * All segments run in one launch of the batch kernel (one work item per
+ * 16384-element chunk of every segment).  Uses a per-stream library
+ * workspace (allocated on first use).  Errors as optigpu_reduce_sum_ex. */
+optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets, int32_t nseg,
+                                        optigpu_dtype dtype, void *out, uint32_t flags,
+                                        optigpu_stream_t stream);
 
 /* Allocates (or grows) the workspace `stream` needs for sums of up to n
  * elements, so that later sums on that stream -- for example inside a CUDA

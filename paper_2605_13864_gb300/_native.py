@@ -47,10 +47,12 @@ SIGNATURES = {
     "optigpu_transpose_tma_eligible": (_ci, [_vp, _vp, _i64, _i64, _ci]),
     "optigpu_transpose_strided": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _ci, _vp]),
     "optigpu_transpose_batched": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _i64, _ci, _vp]),
+    "optigpu_transpose_inplace": (_ci, [_vp, _i64, _ci, _vp]),
     "optigpu_reduce_sum": (_ci, [_vp, _i64, _ci, _vp, _vp]),
     "optigpu_reduce_sum_ex": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_reserve": (_ci, [_i64, _vp]),
+    "optigpu_reduce_segmented": (_ci, [_vp, _vp, ctypes.c_int32, _ci, _vp, _u32, _vp]),
     "optigpu_transpose_host": (_ci, [_vp, _vp, _i64, _i64, _ci, _vp]),
     "optigpu_reduce_sum_host": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_batch_plan_create": (_ci, [_vp, ctypes.c_int32, _u32, ctypes.POINTER(_vp)]),

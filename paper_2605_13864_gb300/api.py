@@ -62,6 +62,16 @@ def transpose(src: torch.Tensor, out: torch.Tensor | None = None, kernel: str = 
     return out
 
 
+def transpose_inplace(a: torch.Tensor, stream=None) -> torch.Tensor:
+    """Transposes the square contiguous CUDA tensor ``a`` in place."""
+    if a.dim() != 2 or a.shape[0] != a.shape[1] or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("transpose_inplace expects a square contiguous CUDA tensor")
+    st = N.lib().optigpu_transpose_inplace(a.data_ptr() if a.numel() else None, int(a.shape[0]),
+                                           dtype_code(a.dtype), _stream_ptr(stream))
+    N.check(st, "optigpu_transpose_inplace")
+    return a
+
+
 def transpose_batched(src: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """(batch, rows, cols) CUDA tensor -> (batch, cols, rows): each matrix
     transposed, in one launch."""
@@ -119,6 +129,25 @@ def reduce_reserve(n: int, stream=None) -> None:
     """Pre-allocates the sum workspace of ``stream`` for up to ``n`` elements
     (do this before capturing sums into a CUDA graph)."""
     N.check(N.lib().optigpu_reduce_reserve(int(n), _stream_ptr(stream)), "optigpu_reduce_reserve")
+
+
+def reduce_segmented(x: torch.Tensor, offsets, compensated: bool = False, stream=None) -> torch.Tensor:
+    """Sums of x[offsets[s]:offsets[s+1]] for every segment, in one launch;
+    int64 results for int32 input, float64 otherwise (on the device)."""
+    import ctypes
+    import numpy as np
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("reduce_segmented expects a contiguous CUDA tensor")
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nseg = offs.size - 1
+    odt = torch.int64 if x.dtype == torch.int32 else torch.float64
+    out = torch.empty(max(nseg, 0), dtype=odt, device=x.device)
+    flags = N.REDUCE_COMPENSATED if compensated else N.REDUCE_PLAIN
+    st = N.lib().optigpu_reduce_segmented(x.data_ptr() if x.numel() else None, offs.ctypes.data,
+                                          nseg, dtype_code(x.dtype), out.data_ptr() if nseg else None, flags,
+                                          _stream_ptr(stream))
+    N.check(st, "optigpu_reduce_segmented")
+    return out
 
 
 def tma_eligible(src: torch.Tensor, dst: torch.Tensor) -> bool:

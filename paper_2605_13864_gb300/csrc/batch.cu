@@ -649,3 +649,69 @@ void optigpu_batch_plan_destroy(optigpu_batch_plan *plan)
 }
 
 } // extern "C"
+
+// ------------------------------------------------------------ segmented sums
+
+extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets, int32_t nseg,
+                                                   optigpu_dtype dtype, void *out, uint32_t flags,
+                                                   optigpu_stream_t stream)
+{
+    using namespace optigpu;
+    if (!dtype_valid(int(dtype)))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce_segmented: unknown dtype");
+    if (flags & ~OPTIGPU_REDUCE_COMPENSATED)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: unknown flag bits");
+    if (nseg < 0 || (nseg > 0 && (!offsets || !out)))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: bad segment table or output");
+    if (nseg == 0)
+        return OPTIGPU_OK;
+    if (reinterpret_cast<uintptr_t>(out) % 8)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: out must be 8-byte aligned");
+    if (offsets[0] < 0)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: negative offset");
+    for (int32_t s = 0; s < nseg; ++s)
+        if (offsets[s + 1] < offsets[s] || offsets[s + 1] > (int64_t(1) << 40))
+            return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: offsets must be non-decreasing and < 2^40");
+    const size_t es = esize_of(dtype);
+    if (offsets[nseg] > offsets[0] && (!src || reinterpret_cast<uintptr_t>(src) % es))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: src must be non-null and element-aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<optigpu_desc> descs(static_cast<size_t>(nseg));
+    for (int32_t k = 0; k < nseg; ++k) {
+        optigpu_desc &d = descs[size_t(k)];
+        d.op = OPTIGPU_OP_REDUCE;
+        d.dtype = int32_t(dtype);
+        d.src = static_cast<const char *>(src) + offsets[k] * int64_t(es);
+        d.dst = static_cast<char *>(out) + 8 * size_t(k);
+        d.rows = offsets[k + 1] - offsets[k];
+        d.cols = 1;
+    }
+    // Empty segments have no chunk: clear every result first.
+    optigpu_status st = check_cuda(cudaMemsetAsync(out, 0, 8 * size_t(nseg), s), "reduce_segmented: clear out");
+    if (st != OPTIGPU_OK)
+        return st;
+    BatchTables t;
+    const int config = 0;
+    if ((st = batch_tables(descs.data(), nseg, batch_tile(config), t)) != OPTIGPU_OK)
+        return st;
+    if (t.items == 0)
+        return OPTIGPU_OK;
+    const BatchLayout L = batch_layout(nseg, t.items, t.chunks);
+    void *ws = nullptr;
+    if ((st = stream_workspace(s, L.total, &ws, 1)) != OPTIGPU_OK)
+        return st;
+    // One host image of [instances | item map], copied in one call (pageable
+    // source: the copy is staged before cudaMemcpyAsync returns).
+    std::vector<char> image(L.off_part - L.off_inst);
+    std::memcpy(image.data(), t.insts.data(), sizeof(BatchInst) * t.insts.size());
+    std::memcpy(image.data() + (L.off_items - L.off_inst), t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size());
+    char *base = static_cast<char *>(ws);
+    if ((st = check_cuda(cudaMemcpyAsync(base + L.off_inst, image.data(), image.size(), cudaMemcpyHostToDevice, s),
+                         "reduce_segmented: upload tables")) != OPTIGPU_OK)
+        return st;
+    return batch_launch(config, reinterpret_cast<BatchInst *>(base + L.off_inst),
+                        reinterpret_cast<uint32_t *>(base + L.off_items), t.items,
+                        reinterpret_cast<unsigned long long *>(base + L.off_queue),
+                        reinterpret_cast<unsigned *>(base + L.off_done), base + L.off_part,
+                        (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr);
+}

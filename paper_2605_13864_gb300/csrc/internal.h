@@ -51,7 +51,9 @@ uint64_t wait_limit_ns();
 // until a later call on the same stream asks for more bytes (then it is
 // reallocated) or optigpu_release_workspaces() runs.  A new buffer is cleared
 // to zero (on `stream`), so counters kept in it start at 0.
-optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr);
+// `slot` separates workspaces with different layouts on one stream (0: the
+// single-call sum; 1: segmented sums).
+optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, int slot = 0);
 
 // Device address of host memory [p, p + bytes) when it is page-locked and
 // mapped for the device (checked at both ends of the range), else nullptr.

@@ -28,7 +28,20 @@ struct Workspace {
     void *ptr = nullptr;
     size_t bytes = 0;
 };
-std::map<std::pair<int, cudaStream_t>, Workspace> g_workspaces;
+struct WsKey {
+    int device;
+    cudaStream_t stream;
+    int slot;
+    bool operator<(const WsKey &o) const
+    {
+        if (device != o.device)
+            return device < o.device;
+        if (stream != o.stream)
+            return stream < o.stream;
+        return slot < o.slot;
+    }
+};
+std::map<WsKey, Workspace> g_workspaces;
 
 uint64_t g_wait_limit_ns = 0;
 
@@ -100,14 +113,14 @@ uint64_t wait_limit_ns()
     return g_wait_limit_ns;
 }
 
-optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr)
+optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, int slot)
 {
     int dev = -1;
     optigpu_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (st != OPTIGPU_OK)
         return st;
     std::lock_guard<std::mutex> lk(g_mu);
-    Workspace &ws = g_workspaces[{dev, stream}];
+    Workspace &ws = g_workspaces[WsKey{dev, stream, slot}];
     if (ws.bytes < bytes) {
         if (ws.ptr) {
             // The old buffer may still be in use by work queued on `stream`.
@@ -287,7 +300,7 @@ optigpu_status optigpu_release_workspaces(void)
         return st;
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_workspaces.begin(); it != g_workspaces.end();) {
-        if (it->first.first == dev) {
+        if (it->first.device == dev) {
             cudaFree(it->second.ptr);
             it = g_workspaces.erase(it);
         } else {

@@ -76,6 +76,56 @@ transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t 
     }
 }
 
+// ---------------------------------------------------------------- in place
+
+// In-place transpose of an n x n matrix: CTA p owns the tile pair (r, c) and
+// (c, r) of the lower triangle (p = r (r + 1) / 2 + c, c <= r), loads both
+// 64 x 64 tiles into padded shared tiles, and writes each back transposed in
+// the other's place (a diagonal tile onto itself).  Every element belongs to
+// exactly one pair and is read before it is written, so there is no race.
+template <typename T>
+__global__ void __launch_bounds__(256)
+transpose_inplace_kernel(T *__restrict__ a, int64_t n, int64_t pairs)
+{
+    constexpr int TS = 64, PAD = sizeof(T) == 4 ? 1 : 2;
+    __shared__ T tile[2][TS][TS + PAD];
+    const int x = threadIdx.x & (TS - 1), y0 = threadIdx.x >> 6; // 64 x 4 threads
+    for (int64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
+        // r = largest integer with r (r + 1) / 2 <= p.
+        int64_t r = int64_t((sqrt(8.0 * double(p) + 1.0) - 1.0) * 0.5);
+        while (r * (r + 1) / 2 > p)
+            --r;
+        while ((r + 1) * (r + 2) / 2 <= p)
+            ++r;
+        const int64_t c = p - r * (r + 1) / 2;
+        const bool diag = (r == c);
+        // Tile 0 = block (r, c), tile 1 = block (c, r).
+        for (int k = 0; k < TS; k += 4) {
+            const int64_t i0 = r * TS + y0 + k, j0 = c * TS + x;
+            if (i0 < n && j0 < n)
+                tile[0][y0 + k][x] = a[i0 * n + j0];
+            if (!diag) {
+                const int64_t i1 = c * TS + y0 + k, j1 = r * TS + x;
+                if (i1 < n && j1 < n)
+                    tile[1][y0 + k][x] = a[i1 * n + j1];
+            }
+        }
+        __syncthreads();
+        // Block (c, r) receives tile 0 transposed; block (r, c) tile 1.
+        for (int k = 0; k < TS; k += 4) {
+            const int64_t i1 = c * TS + y0 + k, j1 = r * TS + x;
+            if (i1 < n && j1 < n)
+                a[i1 * n + j1] = tile[0][x][y0 + k];
+            if (!diag) {
+                const int64_t i0 = r * TS + y0 + k, j0 = c * TS + x;
+                if (i0 < n && j0 < n)
+                    a[i0 * n + j0] = tile[1][x][y0 + k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // --------------------------------------------------------------------- tma
 
 __device__ __forceinline__ uint32_t word_of(const uint4 &v, int j)
@@ -633,6 +683,32 @@ optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst
 {
     return transpose_dispatch_pitched(src, lds, dst, ldd, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO,
                                       static_cast<cudaStream_t>(stream));
+}
+
+optigpu_status optigpu_transpose_inplace(void *a, int64_t n, optigpu_dtype dtype, optigpu_stream_t stream)
+{
+    if (!dtype_valid(int(dtype)))
+        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_inplace: unknown dtype");
+    if (n < 0 || n > (int64_t(1) << 30))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_inplace: n out of range [0, 2^30]");
+    if (n <= 1)
+        return OPTIGPU_OK;
+    const size_t es = esize_of(dtype);
+    if (!a || reinterpret_cast<uintptr_t>(a) % es)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_inplace: null or misaligned pointer");
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const int64_t nt = (n + 63) / 64;
+    const int64_t pairs = nt * (nt + 1) / 2;
+    const int64_t grid = std::min<int64_t>(pairs, int64_t(8) * dev.num_sms);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (es == 4)
+        transpose_inplace_kernel<uint32_t><<<unsigned(grid), 256, 0, s>>>(static_cast<uint32_t *>(a), n, pairs);
+    else
+        transpose_inplace_kernel<uint16_t><<<unsigned(grid), 256, 0, s>>>(static_cast<uint16_t *>(a), n, pairs);
+    return check_cuda(cudaGetLastError(), "launch transpose in place");
 }
 
 optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, void *dst, int64_t stride_dst,

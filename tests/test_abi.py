@@ -220,3 +220,25 @@ def test_batched_transpose_validation(lib):
     assert f(FAKE, 16, FAKE + (1 << 30), 16, -1, 4, 4, N.FLOAT32, None) == N.ERR_INVALID_ARG
     assert f(None, 16, None, 16, 0, 4, 4, N.FLOAT32, None) == N.OK
     assert f(FAKE, 16, FAKE + (1 << 30), 16, 2, 4, 4, 12, None) == N.ERR_UNSUPPORTED_DTYPE
+
+
+def test_segmented_validation(lib):
+    import numpy as np
+    f = lib.optigpu_reduce_segmented
+    bad = np.array([0, 5, 3], dtype=np.int64)          # decreasing
+    assert f(FAKE, bad.ctypes.data, 2, N.FLOAT32, FAKE, 0, None) == N.ERR_INVALID_ARG
+    neg = np.array([-1, 5], dtype=np.int64)
+    assert f(FAKE, neg.ctypes.data, 1, N.FLOAT32, FAKE, 0, None) == N.ERR_INVALID_ARG
+    ok = np.array([0, 5], dtype=np.int64)
+    assert f(FAKE, ok.ctypes.data, 1, N.FLOAT32, FAKE + 4, 0, None) == N.ERR_INVALID_ARG   # out misaligned
+    assert f(FAKE, ok.ctypes.data, 1, 19, FAKE, 0, None) == N.ERR_UNSUPPORTED_DTYPE
+    assert f(None, None, 0, N.FLOAT32, None, 0, None) == N.OK
+
+
+def test_inplace_validation(lib):
+    f = lib.optigpu_transpose_inplace
+    assert f(None, -1, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert f(None, 5, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert f(FAKE + 2, 5, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert f(None, 1, N.FLOAT32, None) == N.OK
+    assert f(FAKE, 5, 33, None) == N.ERR_UNSUPPORTED_DTYPE

@@ -58,3 +58,50 @@ def test_transpose_batched_with_gaps(dtype, batch, rows, cols, gap_s, gap_d):
         assert np.array_equal(got[b * sd:b * sd + n].reshape(cols, rows), bits(oracle.transpose(m)))
         tail = got[b * sd + n:(b + 1) * sd]
         assert (tail.view(np.uint16 if tail.dtype == np.uint16 else np.uint32) == 0x2B2B).all()
+
+
+@pytest.mark.parametrize("compensated", [False, True])
+@pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16"])
+def test_reduce_segmented_matches_oracle_and_single_calls(dtype, compensated):
+    rng = np.random.default_rng(51)
+    lens = [0, 1, 7, 16384, 16385, 0, 50000, 3, 100000, 0]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    a = workloads.vector(int(offs[-1]), dtype, seed=52)
+    d = to_device(a, dtype)
+    got = api.reduce_segmented(d, offs, compensated=compensated).cpu().numpy()
+    want = oracle.segmented_sums(a, offs, dtype)
+    for s in range(len(lens)):
+        seg = a[offs[s]:offs[s + 1]]
+        if dtype == "int32":
+            assert int(got[s]) == want[s]
+        else:
+            tol = 1e-6 * oracle.sum_abs_f64(seg, dtype) + 1e-300 if seg.size else 0.0
+            assert abs(float(got[s]) - want[s]) <= tol
+        if seg.size:
+            single = api.reduce_sum(d[offs[s]:offs[s + 1]], compensated=compensated).item()
+            assert single == got[s]          # the same bits alone and segmented
+        else:
+            assert got[s] == 0
+
+
+def test_reduce_segmented_many_small_segments():
+    rng = np.random.default_rng(53)
+    lens = rng.integers(0, 300, size=5000)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    a = workloads.vector(int(offs[-1]), "int32", seed=54)
+    got = api.reduce_segmented(to_device(a, "int32"), offs).cpu().numpy()
+    assert got.tolist() == oracle.segmented_sums(a, offs)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16", "int32"])
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128, 200, 1000, 4100])
+def test_transpose_inplace(dtype, n):
+    a = workloads.matrix(n, n, dtype, seed=n)
+    d = to_device(a, dtype)
+    api.transpose_inplace(d)
+    torch.cuda.synchronize()
+    api.stream_status()
+    want = oracle.transpose_inplace(np.ascontiguousarray(a).copy())
+    assert np.array_equal(to_host_bits(d), bits(want))
+    api.transpose_inplace(d)  # twice is the identity
+    assert np.array_equal(to_host_bits(d), bits(a))
