@@ -189,6 +189,30 @@ optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets,
                                         optigpu_dtype dtype, void *out, uint32_t flags,
                                         optigpu_stream_t stream);
 
+/* Inclusive prefix sums: dst[i] = src[0] + ... + src[i] (the thesis names
+ * parallel prefix sum as future work, Sec. 9).
+ *   int32 input    -> dst holds int64 values (exact).
+ *   float input    -> dst holds float32 values (fp32, bf16 and fp16 input):
+ *                     FP32 inside each 4096-element sub-block, FP64 carries
+ *                     between sub-blocks and chunks; within 1e-6 of the sum
+ *                     of |x| over the prefix.
+ * Three launches in a fixed order (chunk sums, carries, chunk scans), so the
+ * result is bit-identical from run to run.  src and dst must not overlap;
+ * n in [0, 2^40].  Uses a per-stream library workspace of 16 bytes per
+ * 16384 elements.  Errors as optigpu_reduce_sum_ex, plus OVERLAP. */
+optigpu_status optigpu_scan_inclusive(const void *src, void *dst, int64_t n,
+                                      optigpu_dtype dtype, optigpu_stream_t stream);
+
+/* Histogram of int32 values (the thesis names histograms as future work,
+ * Sec. 9): counts[b] = number of i with lo + b*width <= src[i] <
+ * lo + (b+1)*width, for b < nbins; values outside are not counted.
+ *   counts  device array of nbins int64, overwritten (zeroed, then counted).
+ *   width >= 1, 1 <= nbins <= 2^26, |lo| and width <= 2^40.
+ * Per-CTA shared-memory counters (nbins <= 12288) merged with integer
+ * atomics; exact, so bit-exact against any correct count. */
+optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, int64_t lo, int64_t width,
+                                     int32_t nbins, int64_t *counts, optigpu_stream_t stream);
+
 /* Allocates (or grows) the workspace `stream` needs for sums of up to n
  * elements, so that later sums on that stream -- for example inside a CUDA
  * graph capture -- allocate nothing.  INVALID_ARG for n < 0, OOM on

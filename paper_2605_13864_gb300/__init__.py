@@ -9,6 +9,6 @@ Importing the package does not load the CUDA library; the first operation
 does, and raises if the library cannot be built or loaded.
 """
 from ._native import OptigpuError, load  # noqa: F401
-from .api import (BatchPlan, Server, autotune, reduce_reserve, reduce_segmented, reduce_sum, release_workspaces,  # noqa: F401
+from .api import (BatchPlan, Server, autotune, histogram, reduce_reserve, reduce_segmented, reduce_sum, scan, release_workspaces,  # noqa: F401
                   set_wait_limit_ns, stream_status, tma_eligible, transpose, transpose_batched, transpose_inplace, tune_configs,
                   tune_select, tune_selected)

@@ -53,6 +53,8 @@ SIGNATURES = {
     "optigpu_reduce_sum_noalloc": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_reduce_reserve": (_ci, [_i64, _vp]),
     "optigpu_reduce_segmented": (_ci, [_vp, _vp, ctypes.c_int32, _ci, _vp, _u32, _vp]),
+    "optigpu_scan_inclusive": (_ci, [_vp, _vp, _i64, _ci, _vp]),
+    "optigpu_histogram_i32": (_ci, [_vp, _i64, _i64, _i64, ctypes.c_int32, _vp, _vp]),
     "optigpu_transpose_host": (_ci, [_vp, _vp, _i64, _i64, _ci, _vp]),
     "optigpu_reduce_sum_host": (_ci, [_vp, _i64, _ci, _vp, _u32, _vp]),
     "optigpu_batch_plan_create": (_ci, [_vp, ctypes.c_int32, _u32, ctypes.POINTER(_vp)]),

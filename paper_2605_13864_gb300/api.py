@@ -131,6 +131,34 @@ def reduce_reserve(n: int, stream=None) -> None:
     N.check(N.lib().optigpu_reduce_reserve(int(n), _stream_ptr(stream)), "optigpu_reduce_reserve")
 
 
+def scan(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Inclusive prefix sums of a contiguous CUDA tensor (flattened): int64
+    for int32 input, float32 for float input."""
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("scan expects a contiguous CUDA tensor")
+    odt = torch.int64 if x.dtype == torch.int32 else torch.float32
+    if out is None:
+        out = torch.empty(x.numel(), dtype=odt, device=x.device)
+    elif out.dtype != odt or out.numel() != x.numel() or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {odt} tensor of x.numel() elements")
+    st = N.lib().optigpu_scan_inclusive(x.data_ptr() if x.numel() else None, out.data_ptr() if x.numel() else None,
+                                        x.numel(), dtype_code(x.dtype), _stream_ptr(stream))
+    N.check(st, "optigpu_scan_inclusive")
+    return out
+
+
+def histogram(x: torch.Tensor, lo: int, width: int, nbins: int, stream=None) -> torch.Tensor:
+    """int64 counts of the int32 values of ``x`` in ``nbins`` bins of
+    ``width`` integers starting at ``lo`` (on the device)."""
+    if not x.is_cuda or x.dtype != torch.int32 or not x.is_contiguous():
+        raise ValueError("histogram expects a contiguous int32 CUDA tensor")
+    counts = torch.empty(nbins, dtype=torch.int64, device=x.device)
+    st = N.lib().optigpu_histogram_i32(x.data_ptr() if x.numel() else None, x.numel(), int(lo), int(width),
+                                       int(nbins), counts.data_ptr(), _stream_ptr(stream))
+    N.check(st, "optigpu_histogram_i32")
+    return counts
+
+
 def reduce_segmented(x: torch.Tensor, offsets, compensated: bool = False, stream=None) -> torch.Tensor:
     """Sums of x[offsets[s]:offsets[s+1]] for every segment, in one launch;
     int64 results for int32 input, float64 otherwise (on the device)."""

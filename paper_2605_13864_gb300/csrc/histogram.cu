@@ -1,0 +1,122 @@
+// histogram.cu -- counts of int32 values in equal-width integer bins
+// (the thesis names histograms as future work, Sec. 9):
+//   counts[b] = #{ i : lo + b*width <= src[i] < lo + (b+1)*width },  b < nbins.
+//
+// Each CTA of a persistent grid keeps its own copy of the histogram in shared
+// memory (32-bit counters, shared-memory atomics), walks the input with
+// 16-byte loads (grid-stride), and finally adds its non-zero counters into
+// the int64 result with one global integer atomic each.  Counting is exact
+// whatever the order, so the result is bit-exact.  Histograms with more bins
+// than fit in shared memory count directly with global atomics.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace optigpu {
+namespace {
+
+constexpr int kHistThreads = 512;
+constexpr int kSmemBins = 12288; // 48 KiB of 32-bit counters
+
+struct BinRule {
+    int64_t lo;
+    int64_t width;
+    int64_t nbins;
+    int shift; // log2(width) when width is a power of two, else -1
+
+    __device__ __forceinline__ int64_t bin(int32_t x) const
+    {
+        const int64_t d = int64_t(x) - lo;
+        if (d < 0)
+            return -1;
+        const int64_t b = shift >= 0 ? (d >> shift) : d / width;
+        return b < nbins ? b : -1;
+    }
+};
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kHistThreads)
+histogram_kernel(const int32_t *__restrict__ src, int64_t n, BinRule rule, unsigned long long *counts, int vec_ok)
+{
+    extern __shared__ unsigned int local[];
+    if (SMEM) {
+        for (int64_t b = threadIdx.x; b < rule.nbins; b += kHistThreads)
+            local[b] = 0u;
+        __syncthreads();
+    }
+    auto count = [&](int32_t x) {
+        const int64_t b = rule.bin(x);
+        if (b >= 0) {
+            if (SMEM)
+                atomicAdd(&local[b], 1u);
+            else
+                atomicAdd(&counts[b], 1ull);
+        }
+    };
+    const int64_t tid = int64_t(blockIdx.x) * kHistThreads + threadIdx.x;
+    const int64_t stride = int64_t(gridDim.x) * kHistThreads;
+    if (vec_ok) {
+        const int64_t nv = n / 4;
+        const int4 *v = reinterpret_cast<const int4 *>(src);
+        for (int64_t i = tid; i < nv; i += stride) {
+            const int4 q = __ldcs(v + i);
+            count(q.x);
+            count(q.y);
+            count(q.z);
+            count(q.w);
+        }
+        for (int64_t i = nv * 4 + tid; i < n; i += stride)
+            count(src[i]);
+    } else {
+        for (int64_t i = tid; i < n; i += stride)
+            count(src[i]);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int64_t b = threadIdx.x; b < rule.nbins; b += kHistThreads)
+            if (local[b])
+                atomicAdd(&counts[b], static_cast<unsigned long long>(local[b]));
+    }
+}
+
+} // namespace
+} // namespace optigpu
+
+using namespace optigpu;
+
+extern "C" optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, int64_t lo, int64_t width,
+                                                int32_t nbins, int64_t *counts, optigpu_stream_t stream)
+{
+    if (n < 0 || width < 1 || nbins < 1 || nbins > (1 << 26))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "histogram: need n >= 0, width >= 1, 1 <= nbins <= 2^26");
+    if (!counts || reinterpret_cast<uintptr_t>(counts) % 8 || (n > 0 && (!src || reinterpret_cast<uintptr_t>(src) % 4)))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "histogram: null or misaligned pointer");
+    if (lo < -(int64_t(1) << 40) || lo > (int64_t(1) << 40) || width > (int64_t(1) << 40))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "histogram: lo and width must lie within +-2^40");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    optigpu_status st = check_cuda(cudaMemsetAsync(counts, 0, 8 * size_t(nbins), s), "histogram: clear counts");
+    if (st != OPTIGPU_OK || n == 0)
+        return st;
+    DeviceInfo dev;
+    if ((st = current_device(dev)) != OPTIGPU_OK)
+        return st;
+    BinRule rule{lo, width, nbins, -1};
+    if ((width & (width - 1)) == 0) {
+        int l = 0;
+        while ((int64_t(1) << l) < width)
+            ++l;
+        rule.shift = l;
+    }
+    const bool smem = nbins <= kSmemBins;
+    const size_t smem_bytes = smem ? sizeof(unsigned) * size_t(nbins) : 0;
+    const int per_sm = smem ? std::max(1, int((200u * 1024u) / std::max<size_t>(smem_bytes + 1024, 16384))) : 4;
+    const int64_t want = (n + int64_t(kHistThreads) * 16 - 1) / (int64_t(kHistThreads) * 16);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::min(per_sm, 4)) * dev.num_sms));
+    const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
+    auto *c = reinterpret_cast<unsigned long long *>(counts);
+    if (smem)
+        histogram_kernel<true><<<unsigned(grid), kHistThreads, smem_bytes, s>>>(src, n, rule, c, vec_ok);
+    else
+        histogram_kernel<false><<<unsigned(grid), kHistThreads, 0, s>>>(src, n, rule, c, vec_ok);
+    return check_cuda(cudaGetLastError(), "launch histogram");
+}

@@ -242,3 +242,21 @@ def test_inplace_validation(lib):
     assert f(FAKE + 2, 5, N.FLOAT32, None) == N.ERR_INVALID_ARG
     assert f(None, 1, N.FLOAT32, None) == N.OK
     assert f(FAKE, 5, 33, None) == N.ERR_UNSUPPORTED_DTYPE
+
+
+def test_scan_validation(lib):
+    f = lib.optigpu_scan_inclusive
+    assert f(FAKE, FAKE + 16, 100, N.FLOAT32, None) == N.ERR_OVERLAP
+    assert f(FAKE, FAKE + (1 << 20) + 4, 100, N.INT32, None) == N.ERR_INVALID_ARG   # int64 out misaligned
+    assert f(None, None, 0, N.FLOAT32, None) == N.OK
+    assert f(FAKE, FAKE + (1 << 20), -1, N.FLOAT32, None) == N.ERR_INVALID_ARG
+    assert f(FAKE, FAKE + (1 << 20), 5, 9, None) == N.ERR_UNSUPPORTED_DTYPE
+
+
+def test_histogram_validation(lib):
+    f = lib.optigpu_histogram_i32
+    assert f(FAKE, 10, 0, 0, 4, FAKE, None) == N.ERR_INVALID_ARG        # width 0
+    assert f(FAKE, 10, 0, 1, 0, FAKE, None) == N.ERR_INVALID_ARG        # no bins
+    assert f(FAKE, 10, 0, 1, 4, FAKE + 4, None) == N.ERR_INVALID_ARG    # counts misaligned
+    assert f(FAKE + 2, 10, 0, 1, 4, FAKE, None) == N.ERR_INVALID_ARG    # src misaligned
+    assert f(FAKE, 10, 1 << 41, 1, 4, FAKE, None) == N.ERR_INVALID_ARG

@@ -105,3 +105,58 @@ def test_transpose_inplace(dtype, n):
     assert np.array_equal(to_host_bits(d), bits(want))
     api.transpose_inplace(d)  # twice is the identity
     assert np.array_equal(to_host_bits(d), bits(a))
+
+
+def _abs_bits(a, dtype):
+    if dtype in ("bfloat16", "float16"):
+        return (a & np.uint16(0x7FFF)).astype(np.uint16)
+    return np.abs(a)
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16", "float16"])
+@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 4095, 4096, 4097, 16384, 16385, 3 * 16384 + 77, 1 << 20])
+def test_scan_matches_oracle(dtype, n):
+    a = workloads.vector(n, dtype, seed=n + 3)
+    got = api.scan(to_device(a, dtype))
+    torch.cuda.synchronize()
+    api.stream_status()
+    want = oracle.scan(a, dtype)
+    g = got.cpu().numpy()
+    if dtype == "int32":
+        assert np.array_equal(g, want)
+    else:
+        scale = oracle.scan(_abs_bits(a, dtype), dtype)
+        err = np.abs(g.astype(np.float64) - want)
+        assert (err <= 1e-6 * scale + 1e-30).all(), (n, float(err.max()))
+
+
+def test_scan_closed_form_and_repeatability():
+    n = (1 << 22) + 5
+    a = np.arange(n, dtype=np.int64).astype(np.int32) % 1000
+    d = to_device(np.ascontiguousarray(a), "int32")
+    g1 = api.scan(d).cpu().numpy()
+    assert np.array_equal(g1, oracle.scan(a))
+    assert g1[-1] == oracle.sum_i64(a)
+    f = workloads.vector(3 << 20, "float32", seed=8)
+    df = to_device(f, "float32")
+    r1 = api.scan(df).cpu().numpy()
+    r2 = api.scan(df).cpu().numpy()
+    assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))   # bit-identical runs
+
+
+@pytest.mark.parametrize("lo,width,nbins", [(0, 1, 100), (-50, 7, 29), (-1000, 1, 2001), (0, 16, 4096),
+                                            (-2**31, 2**24, 256), (5, 3, 20000), (0, 1, 1)])
+@pytest.mark.parametrize("n", [0, 1, 1000, 123457, 1 << 22])
+def test_histogram_matches_oracle(lo, width, nbins, n):
+    rng = np.random.default_rng(n + nbins)
+    a = rng.integers(-1200, 1200, size=n, dtype=np.int32)
+    got = api.histogram(to_device(a, "int32"), lo, width, nbins).cpu().numpy()
+    assert np.array_equal(got, oracle.histogram_i32(a, lo, width, nbins))
+
+
+def test_histogram_unaligned_source_and_full_range():
+    a = np.random.default_rng(3).integers(-2**31, 2**31 - 1, size=100003, dtype=np.int64).astype(np.int32)
+    d = to_device(a, "int32", offset_elems=1)
+    got = api.histogram(d, -2**31, 2**28, 16).cpu().numpy()
+    assert np.array_equal(got, oracle.histogram_i32(a, -2**31, 2**28, 16))
+    assert got.sum() == a.size
