@@ -414,6 +414,59 @@ def measure_precision():
     return res
 
 
+def measure_next(reps: int = 10):
+    """The neighbouring problems at roofline scale, CUDA-event timed:
+    batched transpose (64 x 2048^2 fp32), in-place transpose (16384^2 fp32),
+    segmented sums (2^28 fp32 in 16384 segments), inclusive scans (2^28 int32
+    -> int64, 2^28 fp32 -> fp32) and the int32 histogram (2^28 values,
+    4096 bins).  Bytes follow the same convention: every input byte read
+    once plus every output byte written once."""
+    import torch
+    from paper_2605_13864_gb300 import api
+
+    peak, _ = _peaks()
+    res = {}
+
+    def timed(name, fn, nbytes):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = nbytes / ms / 1e6
+        res[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 4),
+                     "algorithmic_bytes": int(nbytes)}
+
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(64, 2048, 2048, device="cuda", generator=g)
+    y = torch.empty(64, 2048, 2048, device="cuda")
+    timed("transpose_batched_64x2048x2048_fp32", lambda: api.transpose_batched(x, out=y), 2 * x.numel() * 4)
+    del x, y
+    m = torch.randn(16384, 16384, device="cuda", generator=g)
+    timed("transpose_inplace_16384_fp32", lambda: api.transpose_inplace(m), 2 * m.numel() * 4)
+    del m
+    v = torch.randn(1 << 28, device="cuda", generator=g)
+    lens = np.random.default_rng(6).integers(1, 2 * (1 << 28) // 16384, size=16384)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    offs = np.minimum(offs, 1 << 28)
+    timed("reduce_segmented_2p28_fp32_16384seg", lambda: api.reduce_segmented(v, offs), int(offs[-1]) * 4)
+    out32 = torch.empty(1 << 28, device="cuda")
+    timed("scan_2p28_fp32", lambda: api.scan(v, out=out32), (1 << 28) * 8)
+    del out32
+    vi = torch.randint(0, 4096, (1 << 28,), dtype=torch.int32, device="cuda", generator=g)
+    out64 = torch.empty(1 << 28, dtype=torch.int64, device="cuda")
+    timed("scan_2p28_int32_to_int64", lambda: api.scan(vi, out=out64), (1 << 28) * 12)
+    del out64
+    timed("histogram_2p28_int32_4096bins", lambda: api.histogram(vi, 0, 1, 4096), (1 << 28) * 4)
+    del v, vi
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -569,6 +622,8 @@ def run_gpu(args):
             line["served"] = measure_served()
         if not args.no_precision:
             line["precision"] = measure_precision()
+        if not args.no_next:
+            line["next"] = measure_next()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -633,6 +688,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch)")

@@ -10,11 +10,12 @@
 //   2. carries: one CTA turns the partials into exclusive prefixes (thread t
 //      scans a contiguous run sequentially, then a block scan of the run
 //      totals), carry[c] = partial[0] + ... + partial[c-1];
-//   3. chunk scans: each chunk is scanned in four 4096-element sub-blocks;
-//      thread t owns 16 consecutive elements, scans them sequentially, the
-//      256 thread totals are scanned with warp shuffles and a shared-memory
-//      pass over the 8 warp totals, and every output adds the FP64 carry of
-//      the chunk and of the preceding sub-blocks.
+//   3. chunk scans: each chunk is scanned in four 4096-element sub-blocks,
+//      staged through padded shared memory so that global loads and stores
+//      are coalesced; thread t owns 16 consecutive elements, scans them
+//      sequentially, the 256 thread totals are scanned with warp shuffles and
+//      a shared-memory pass over the 8 warp totals, and every output adds the
+//      FP64 carry of the chunk and of the preceding sub-blocks.
 // int32 input gives exact int64 output.  Float input (fp32, bf16, fp16) is
 // scanned in FP32 inside a sub-block, carried in FP64, and written as fp32.
 #include <algorithm>
@@ -128,7 +129,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_carries_kernel(const P *par
     }
 }
 
-// Phase 3: scan every chunk (persistent grid-stride over chunks).
+// Shared staging of one sub-block.  Element e of the input lives at word
+// e + e / 32 (one pad word per 32): both the coalesced fill (consecutive e
+// across lanes) and the per-thread read of 16 consecutive elements (lanes 16
+// elements apart) hit 32 distinct banks.  8-byte outputs use one pad slot
+// per 16 elements for the same reason.
+__device__ __forceinline__ int pad4(int e) { return e + (e >> 5); }
+__device__ __forceinline__ int pad8(int e) { return e + (e >> 4); }
+
+// Phase 3: scan every chunk (persistent grid-stride over chunks).  Global
+// loads and stores are coalesced (thread t touches elements t + 256 k); the
+// per-thread contiguous runs are gathered from and scattered to shared memory.
 template <int DT>
 __global__ void __launch_bounds__(kScanThreads)
 scan_chunks_kernel(const void *__restrict__ src, void *__restrict__ dst, int64_t n, const void *carries,
@@ -138,29 +149,50 @@ scan_chunks_kernel(const void *__restrict__ src, void *__restrict__ dst, int64_t
     using Acc = typename T::Acc;
     using Carry = typename T::Carry;
     using Out = typename T::Out;
+    constexpr bool kWide = sizeof(Out) == 8;
     __shared__ Acc warp_tot[kScanThreads / 32];
+    __shared__ union {
+        Acc in[kSub + kSub / 32];
+        Out out[kWide ? kSub + kSub / 16 : kSub + kSub / 32];
+    } stage;
     const Carry *carry = static_cast<const Carry *>(carries);
     Out *out = static_cast<Out *>(dst);
+    const int t = threadIdx.x;
     for (int64_t c = blockIdx.x; c < num_chunks; c += gridDim.x) {
         Carry run = carry[c];
         for (int sb = 0; sb < int(kReduceChunk / kSub); ++sb) {
             const int64_t base = c * kReduceChunk + int64_t(sb) * kSub;
             if (base >= n)
                 break; // uniform across the CTA
-            const int64_t first = base + int64_t(threadIdx.x) * kPerThread;
+#pragma unroll
+            for (int k = 0; k < kPerThread; ++k) {
+                const int e = t + k * kScanThreads;
+                stage.in[pad4(e)] = (base + e < n) ? T::load(src, base + e) : Acc(0);
+            }
+            __syncthreads();
             Acc v[kPerThread];
 #pragma unroll
-            for (int e = 0; e < kPerThread; ++e)
-                v[e] = (first + e < n) ? T::load(src, first + e) : Acc(0);
+            for (int j = 0; j < kPerThread; ++j)
+                v[j] = stage.in[pad4(t * kPerThread + j)];
 #pragma unroll
-            for (int e = 1; e < kPerThread; ++e)
-                v[e] += v[e - 1];
+            for (int j = 1; j < kPerThread; ++j)
+                v[j] += v[j - 1];
             Acc total;
             const Acc before = block_exclusive_scan<Acc>(v[kPerThread - 1], warp_tot, &total);
+            // (block_exclusive_scan ends with a barrier: stage.in is free.)
 #pragma unroll
-            for (int e = 0; e < kPerThread; ++e)
-                if (first + e < n)
-                    out[first + e] = T::finish(run, before + v[e]);
+            for (int j = 0; j < kPerThread; ++j) {
+                const int e = t * kPerThread + j;
+                stage.out[kWide ? pad8(e) : pad4(e)] = T::finish(run, before + v[j]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPerThread; ++k) {
+                const int e = t + k * kScanThreads;
+                if (base + e < n)
+                    out[base + e] = stage.out[kWide ? pad8(e) : pad4(e)];
+            }
+            __syncthreads();
             run += Carry(total);
         }
     }
