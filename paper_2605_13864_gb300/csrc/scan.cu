@@ -17,7 +17,9 @@
 //      a shared-memory pass over the 8 warp totals, and every output adds the
 //      FP64 carry of the chunk and of the preceding sub-blocks.
 // int32 input gives exact int64 output.  Float input (fp32, bf16, fp16) is
-// scanned in FP32 inside a sub-block, carried in FP64, and written as fp32.
+// scanned in FP32 inside a sub-block, carried in FP64 between sub-blocks
+// and chunks (the carry reaches each element as an FP32 hi + lo pair), and
+// written as fp32.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -36,44 +38,58 @@ static_assert(kReduceChunk % kSub == 0, "chunks split into whole sub-blocks");
 
 template <int DT>
 struct ScanTraits;
+// FP64 runs at a small fraction of the FP32 rate on this part, so a float
+// carry is split once per sub-block into hi + lo (hi = the carry rounded to
+// FP32, lo = the rounding error, also in FP32) and each output costs two FP32
+// additions: hi + (lo + v), within an FP32 ulp of the exact carry + v.
+struct SplitCarry {
+    float hi, lo;
+};
+
+__device__ __forceinline__ SplitCarry split_carry(double c)
+{
+    const float hi = float(c);
+    return SplitCarry{hi, float(c - double(hi))};
+}
+
 template <>
 struct ScanTraits<OPTIGPU_INT32> {
-    using In = int32_t;
     using Acc = long long; // in-sub-block accumulator
     using Carry = long long;
+    using Split = long long;
     using Out = long long;
     __device__ static Acc load(const void *p, int64_t i) { return static_cast<const int32_t *>(p)[i]; }
-    __device__ static Out finish(Carry c, Acc v) { return c + v; }
+    __device__ static Split split(Carry c) { return c; }
+    __device__ static Out finish(Split c, Acc v) { return c + v; }
+};
+
+struct FloatFinish {
+    using Carry = double;
+    using Split = SplitCarry;
+    using Out = float;
+    __device__ static Split split(Carry c) { return split_carry(c); }
+    __device__ static Out finish(Split c, float v) { return c.hi + (c.lo + v); }
 };
 template <>
-struct ScanTraits<OPTIGPU_FLOAT32> {
+struct ScanTraits<OPTIGPU_FLOAT32> : FloatFinish {
     using Acc = float;
-    using Carry = double;
-    using Out = float;
     __device__ static Acc load(const void *p, int64_t i) { return static_cast<const float *>(p)[i]; }
-    __device__ static Out finish(Carry c, Acc v) { return float(c + double(v)); }
 };
 template <>
-struct ScanTraits<OPTIGPU_BFLOAT16> {
+struct ScanTraits<OPTIGPU_BFLOAT16> : FloatFinish {
     using Acc = float;
-    using Carry = double;
-    using Out = float;
     __device__ static Acc load(const void *p, int64_t i)
     {
         return __uint_as_float(uint32_t(static_cast<const uint16_t *>(p)[i]) << 16);
     }
-    __device__ static Out finish(Carry c, Acc v) { return float(c + double(v)); }
 };
 template <>
-struct ScanTraits<OPTIGPU_FLOAT16> {
+struct ScanTraits<OPTIGPU_FLOAT16> : FloatFinish {
     using Acc = float;
-    using Carry = double;
-    using Out = float;
     __device__ static Acc load(const void *p, int64_t i)
     {
         return __half2float(__ushort_as_half(static_cast<const unsigned short *>(p)[i]));
     }
-    __device__ static Out finish(Carry c, Acc v) { return float(c + double(v)); }
 };
 
 // Block-wide exclusive scan of one value per thread (fixed order: Kogge-Stone
@@ -180,10 +196,11 @@ scan_chunks_kernel(const void *__restrict__ src, void *__restrict__ dst, int64_t
             Acc total;
             const Acc before = block_exclusive_scan<Acc>(v[kPerThread - 1], warp_tot, &total);
             // (block_exclusive_scan ends with a barrier: stage.in is free.)
+            const typename T::Split sc = T::split(run);
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j) {
                 const int e = t * kPerThread + j;
-                stage.out[kWide ? pad8(e) : pad4(e)] = T::finish(run, before + v[j]);
+                stage.out[kWide ? pad8(e) : pad4(e)] = T::finish(sc, before + v[j]);
             }
             __syncthreads();
 #pragma unroll
