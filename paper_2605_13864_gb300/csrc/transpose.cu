@@ -37,6 +37,7 @@
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "tma_tile.cuh"
 
 namespace optigpu {
 namespace {
@@ -76,113 +77,7 @@ transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t 
     }
 }
 
-// ---------------------------------------------------------------- in place
-
-// In-place transpose of an n x n matrix: CTA p owns the tile pair (r, c) and
-// (c, r) of the lower triangle (p = r (r + 1) / 2 + c, c <= r), loads both
-// 64 x 64 tiles into padded shared tiles, and writes each back transposed in
-// the other's place (a diagonal tile onto itself).  Every element belongs to
-// exactly one pair and is read before it is written, so there is no race.
-template <typename T>
-__global__ void __launch_bounds__(256)
-transpose_inplace_kernel(T *__restrict__ a, int64_t n, int64_t pairs)
-{
-    constexpr int TS = 64, PAD = sizeof(T) == 4 ? 1 : 2;
-    __shared__ T tile[2][TS][TS + PAD];
-    const int x = threadIdx.x & (TS - 1), y0 = threadIdx.x >> 6; // 64 x 4 threads
-    for (int64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
-        // r = largest integer with r (r + 1) / 2 <= p.
-        int64_t r = int64_t((sqrt(8.0 * double(p) + 1.0) - 1.0) * 0.5);
-        while (r * (r + 1) / 2 > p)
-            --r;
-        while ((r + 1) * (r + 2) / 2 <= p)
-            ++r;
-        const int64_t c = p - r * (r + 1) / 2;
-        const bool diag = (r == c);
-        // Tile 0 = block (r, c), tile 1 = block (c, r).
-        for (int k = 0; k < TS; k += 4) {
-            const int64_t i0 = r * TS + y0 + k, j0 = c * TS + x;
-            if (i0 < n && j0 < n)
-                tile[0][y0 + k][x] = a[i0 * n + j0];
-            if (!diag) {
-                const int64_t i1 = c * TS + y0 + k, j1 = r * TS + x;
-                if (i1 < n && j1 < n)
-                    tile[1][y0 + k][x] = a[i1 * n + j1];
-            }
-        }
-        __syncthreads();
-        // Block (c, r) receives tile 0 transposed; block (r, c) tile 1.
-        for (int k = 0; k < TS; k += 4) {
-            const int64_t i1 = c * TS + y0 + k, j1 = r * TS + x;
-            if (i1 < n && j1 < n)
-                a[i1 * n + j1] = tile[0][x][y0 + k];
-            if (!diag) {
-                const int64_t i0 = r * TS + y0 + k, j0 = c * TS + x;
-                if (i0 < n && j0 < n)
-                    a[i0 * n + j0] = tile[1][x][y0 + k];
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // --------------------------------------------------------------------- tma
-
-__device__ __forceinline__ uint32_t word_of(const uint4 &v, int j)
-{
-    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
-}
-
-// Writes the transpose of the V x V micro-block held in r[0..V) (row i of
-// the block = r[i]) as V 16-byte rows at out, out + pitch, ...
-template <int ESIZE>
-__device__ __forceinline__ void store_transposed(const uint4 *r, uint32_t out, uint32_t pitch);
-
-template <>
-__device__ __forceinline__ void store_transposed<4>(const uint4 *r, uint32_t out, uint32_t pitch)
-{
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        uint4 o = make_uint4(word_of(r[0], j), word_of(r[1], j), word_of(r[2], j), word_of(r[3], j));
-        ptx::sts_v4(out + j * pitch, o);
-    }
-}
-
-template <>
-__device__ __forceinline__ void store_transposed<2>(const uint4 *r, uint32_t out, uint32_t pitch)
-{
-    // Output row j = 2w + h holds column j of the 8 input rows; its word k
-    // packs rows 2k (low half) and 2k+1 (high half).  Selector 0x5410 takes
-    // the low halves of both words, 0x7632 the high halves.
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const unsigned sel = h ? 0x7632u : 0x5410u;
-            uint4 o;
-            o.x = __byte_perm(word_of(r[0], w), word_of(r[1], w), sel);
-            o.y = __byte_perm(word_of(r[2], w), word_of(r[3], w), sel);
-            o.z = __byte_perm(word_of(r[4], w), word_of(r[5], w), sel);
-            o.w = __byte_perm(word_of(r[6], w), word_of(r[7], w), sel);
-            ptx::sts_v4(out + (2 * w + h) * pitch, o);
-        }
-    }
-}
-
-template <int ESIZE, int TR, int TC>
-struct TmaTile {
-    static constexpr int V = 16 / ESIZE;        // elements per 16-byte vector
-    static constexpr int MR = TR / V;           // micro-block rows
-    static constexpr int MC = TC / V;           // micro-block columns
-    static constexpr int THREADS = MR * MC;     // one micro-block per consumer thread
-    static constexpr uint32_t BYTES = TR * TC * ESIZE;
-    static constexpr uint32_t IN_PITCH = TC * ESIZE;  // source tile row
-    static constexpr uint32_t OUT_PITCH = TR * ESIZE; // output tile row
-    static_assert(MR % 8 == 0 && MC % 8 == 0, "micro-block grid must be a multiple of 8");
-    static_assert(IN_PITCH % 128 == 0 && OUT_PITCH % 128 == 0, "tile rows must span whole bank cycles");
-    static_assert(TR <= 256 && TC <= 256, "TMA box dimensions are at most 256");
-    static_assert(THREADS % 32 == 0 && THREADS <= 512, "consumer threads");
-};
 
 // Tile order.  Tile ids run down `group` tile-rows before moving one
 // tile-column right, so the CTAs working at one moment (consecutive ids)
@@ -683,32 +578,6 @@ optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst
 {
     return transpose_dispatch_pitched(src, lds, dst, ldd, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO,
                                       static_cast<cudaStream_t>(stream));
-}
-
-optigpu_status optigpu_transpose_inplace(void *a, int64_t n, optigpu_dtype dtype, optigpu_stream_t stream)
-{
-    if (!dtype_valid(int(dtype)))
-        return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_inplace: unknown dtype");
-    if (n < 0 || n > (int64_t(1) << 30))
-        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_inplace: n out of range [0, 2^30]");
-    if (n <= 1)
-        return OPTIGPU_OK;
-    const size_t es = esize_of(dtype);
-    if (!a || reinterpret_cast<uintptr_t>(a) % es)
-        return fail(OPTIGPU_ERR_INVALID_ARG, "transpose_inplace: null or misaligned pointer");
-    DeviceInfo dev;
-    optigpu_status st = current_device(dev);
-    if (st != OPTIGPU_OK)
-        return st;
-    const int64_t nt = (n + 63) / 64;
-    const int64_t pairs = nt * (nt + 1) / 2;
-    const int64_t grid = std::min<int64_t>(pairs, int64_t(8) * dev.num_sms);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (es == 4)
-        transpose_inplace_kernel<uint32_t><<<unsigned(grid), 256, 0, s>>>(static_cast<uint32_t *>(a), n, pairs);
-    else
-        transpose_inplace_kernel<uint16_t><<<unsigned(grid), 256, 0, s>>>(static_cast<uint16_t *>(a), n, pairs);
-    return check_cuda(cudaGetLastError(), "launch transpose in place");
 }
 
 optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, void *dst, int64_t stride_dst,
