@@ -462,6 +462,13 @@ def measure_next(reps: int = 10):
     offs = np.concatenate([[0], np.cumsum(lens)])
     offs = np.minimum(offs, 1 << 28)
     timed("reduce_segmented_2p28_fp32_16384seg", lambda: api.reduce_segmented(v, offs), int(offs[-1]) * 4)
+    # The same segments as a plan (tables built once, one graph launch per run).
+    outs = torch.empty(len(offs) - 1, dtype=torch.float64, device="cuda")
+    items = [("reduce", v[offs[k]:offs[k + 1]], outs[k]) for k in range(len(offs) - 1)]
+    plan = api.BatchPlan(items)
+    timed("reduce_segmented_2p28_fp32_16384seg_planned", plan.run, int(offs[-1]) * 4)
+    plan.close()
+    del items, outs
     out32 = torch.empty(1 << 28, device="cuda")
     timed("scan_2p28_fp32", lambda: api.scan(v, out=out32), (1 << 28) * 8)
     del out32
