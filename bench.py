@@ -469,13 +469,16 @@ def measure_next(reps: int = 10):
     timed("reduce_segmented_2p28_fp32_16384seg_planned", plan.run, int(offs[-1]) * 4)
     plan.close()
     del items, outs
-    out32 = torch.empty(1 << 28, device="cuda")
-    timed("scan_2p28_fp32", lambda: api.scan(v, out=out32), (1 << 28) * 8)
-    del out32
     vi = torch.randint(0, 4096, (1 << 28,), dtype=torch.int32, device="cuda", generator=g)
+    out32 = torch.empty(1 << 28, device="cuda")
     out64 = torch.empty(1 << 28, dtype=torch.int64, device="cuda")
-    timed("scan_2p28_int32_to_int64", lambda: api.scan(vi, out=out64), (1 << 28) * 12)
-    del out64
+    scan_default = api.tune_selected("scan", torch.float32)
+    for cfg, tag in ((0, ""), (1, "_three_pass")):
+        api.tune_select("scan", torch.float32, cfg)
+        timed("scan_2p28_fp32" + tag, lambda: api.scan(v, out=out32), (1 << 28) * 8)
+        timed("scan_2p28_int32_to_int64" + tag, lambda: api.scan(vi, out=out64), (1 << 28) * 12)
+    api.tune_select("scan", torch.float32, scan_default)
+    del out32, out64
     timed("histogram_2p28_int32_4096bins", lambda: api.histogram(vi, 0, 1, 4096), (1 << 28) * 4)
     del v, vi
     torch.cuda.empty_cache()

@@ -72,7 +72,8 @@ typedef enum {
 typedef enum {
     OPTIGPU_OP_TRANSPOSE = 0,
     OPTIGPU_OP_REDUCE = 1,
-    OPTIGPU_OP_BATCH = 2 /* autotuner only: the batch kernel's configurations */
+    OPTIGPU_OP_BATCH = 2, /* autotuner only: the batch kernel's configurations */
+    OPTIGPU_OP_SCAN = 3   /* autotuner only: single-pass or three-pass inclusive scan */
 } optigpu_op;
 
 /* ------------------------------------------------------------------------ */
@@ -196,10 +197,16 @@ optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets,
  *                     FP32 inside each 4096-element sub-block, FP64 carries
  *                     between sub-blocks and chunks; within 1e-6 of the sum
  *                     of |x| over the prefix.
- * Three launches in a fixed order (chunk sums, carries, chunk scans), so the
- * result is bit-identical from run to run.  src and dst must not overlap;
- * n in [0, 2^40].  Uses a per-stream library workspace of 16 bytes per
- * 16384 elements.  Errors as optigpu_reduce_sum_ex, plus OVERLAP. */
+ * Default: one pass over 4096-element chunks claimed in order; the carry of
+ * chunk c is a sum of aligned power-of-two blocks of earlier chunk totals
+ * (pairwise sums, the blocks of the binary decomposition of c added largest
+ * first), an expression fixed by c, so the result is bit-identical from run
+ * to run (device waits bounded; a wait that gives up is reported by
+ * optigpu_stream_status).  The three-launch form (chunk sums, carries, chunk
+ * scans) is the tuner's configuration 1 (OPTIGPU_OP_SCAN).  src and dst must
+ * not overlap; n in [0, 2^40].  Uses a per-stream library workspace of about
+ * 10 bytes per 1024 elements.  Errors as
+ * optigpu_reduce_sum_ex, plus OVERLAP. */
 optigpu_status optigpu_scan_inclusive(const void *src, void *dst, int64_t n,
                                       optigpu_dtype dtype, optigpu_stream_t stream);
 
@@ -423,7 +430,7 @@ void optigpu_server_destroy(optigpu_server *server);
 /* Number of configurations of `op` for `dtype` (-1 for a bad op or dtype).
  * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel.
  * OPTIGPU_OP_BATCH ignores `dtype`; its selection is the default of new
- * plans. */
+ * plans.  OPTIGPU_OP_SCAN ignores `dtype`: 0 = single pass, 1 = three passes. */
 int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype);
 
 /* Static name of configuration `config`, or NULL if out of range. */

@@ -113,6 +113,7 @@ class ServerStats(ctypes.Structure):
 SERVER_PER_CALL = 4
 BATCH_NO_GRAPH = 2
 OP_BATCH = 2
+OP_SCAN = 3
 
 
 class OptigpuError(RuntimeError):

@@ -199,7 +199,7 @@ def release_workspaces() -> None:
 
 # ---------------------------------------------------------------- autotuning
 
-_OPS = {"transpose": N.OP_TRANSPOSE, "reduce": N.OP_REDUCE, "batch": N.OP_BATCH}
+_OPS = {"transpose": N.OP_TRANSPOSE, "reduce": N.OP_REDUCE, "batch": N.OP_BATCH, "scan": N.OP_SCAN}
 
 
 def tune_configs(op: str, dtype: torch.dtype = torch.float32) -> list[str]:

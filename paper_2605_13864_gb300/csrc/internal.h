@@ -68,6 +68,11 @@ optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDat
 optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
                                     uint64_t stride2_bytes, uint32_t box0, uint32_t box1);
+// Same with a chosen shared-memory swizzle (the 3-D form above uses none).
+optigpu_status encode_tensor_map_3d_swizzled(CUtensorMap *map, void *base, CUtensorMapDataType type,
+                                             uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
+                                             uint64_t stride2_bytes, uint32_t box0, uint32_t box1,
+                                             CUtensorMapSwizzle swizzle);
 
 // Transpose configurations: indices 0 .. n-2 are TMA kernels, n-1 is tile32.
 int transpose_num_configs(size_t esize);
@@ -103,6 +108,12 @@ optigpu_status transpose_dispatch_pitched(const void *src, int64_t lds, void *ds
 // Transpose of a dense b x cols band into dst with row pitch ldd.
 optigpu_status transpose_band_into(const void *band, void *dst, int64_t b, int64_t cols, int64_t ldd, int dtype,
                                    cudaStream_t stream);
+
+// Scan configurations: 0 = single pass (ordered look-back), 1 = three passes.
+int scan_num_configs();
+const char *scan_config_name(int config);
+int scan_selected();
+void scan_select(int config);
 
 // Batch kernel configurations (default of new plans).
 int batch_num_configs();

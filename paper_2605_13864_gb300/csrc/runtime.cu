@@ -178,6 +178,15 @@ optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDat
                                     uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
                                     uint64_t stride2_bytes, uint32_t box0, uint32_t box1)
 {
+    return encode_tensor_map_3d_swizzled(map, base, type, dim0, dim1, dim2, stride1_bytes, stride2_bytes, box0,
+                                         box1, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+optigpu_status encode_tensor_map_3d_swizzled(CUtensorMap *map, void *base, CUtensorMapDataType type,
+                                             uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,
+                                             uint64_t stride2_bytes, uint32_t box0, uint32_t box1,
+                                             CUtensorMapSwizzle swizzle)
+{
     optigpu_status st = encode_entry();
     if (st != OPTIGPU_OK)
         return st;
@@ -186,7 +195,7 @@ optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDat
     const cuuint32_t box[3] = {box0, box1, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(OPTIGPU_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed with CUresult " + std::to_string(int(r)));

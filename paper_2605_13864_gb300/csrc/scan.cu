@@ -2,9 +2,11 @@
 // (the thesis names parallel prefix sum as future work, Sec. 9; the running
 // sum of Listing 2.1's loop, keeping every intermediate value).
 //
-// Three launches, all in a fixed order, so results are bit-identical from run
-// to run (a single-pass decoupled look-back would combine floats in a
-// timing-dependent order):
+// Default: one pass (scan_onepass_kernel below): 4096-element chunks claimed
+// in order, TMA-staged, each carried by a sum of dyadic blocks of earlier
+// chunk totals whose expression depends on the chunk index alone, so results
+// are bit-identical from run to run and no chunk waits on another's carry.
+// The three-launch form, kept as configuration 1, runs in a fixed order too:
 //   1. chunk sums: the sum's own kernel (reduce_band) writes one FP64 / int64
 //      partial per 16384-element chunk;
 //   2. carries: one CTA turns the partials into exclusive prefixes (thread t
@@ -21,11 +23,15 @@
 // and chunks (the carry reaches each element as an FP32 hi + lo pair), and
 // written as fp32.
 #include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
+#include "ptx.cuh"
 #include "reduce_core.cuh"
 
 namespace optigpu {
@@ -49,7 +55,9 @@ struct SplitCarry {
 __device__ __forceinline__ SplitCarry split_carry(double c)
 {
     const float hi = float(c);
-    return SplitCarry{hi, float(c - double(hi))};
+    // An infinite or NaN carry passes through hi alone (inf - inf in lo
+    // would turn an infinite prefix into NaN).
+    return SplitCarry{hi, isfinite(hi) ? float(c - double(hi)) : 0.0f};
 }
 
 template <>
@@ -95,7 +103,16 @@ struct ScanTraits<OPTIGPU_FLOAT16> : FloatFinish {
 // Block-wide exclusive scan of one value per thread (fixed order: Kogge-Stone
 // inside each warp, then the 8 warp totals by warp 0).  Returns the exclusive
 // prefix; *total receives the block total (valid in every thread).
-template <typename T>
+template <int BAR>
+__device__ __forceinline__ void scan_barrier()
+{
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        ptx::named_bar_sync(BAR, kScanThreads);
+}
+
+template <typename T, int BAR = 0>
 __device__ __forceinline__ T block_exclusive_scan(T v, T *warp_tot, T *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -108,7 +125,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *warp_tot, T *total)
     }
     if (lane == 31)
         warp_tot[warp] = incl;
-    __syncthreads();
+    scan_barrier<BAR>();
     if (warp == 0) {
         T w = lane < kScanThreads / 32 ? warp_tot[lane] : T(0);
 #pragma unroll
@@ -120,11 +137,14 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *warp_tot, T *total)
         if (lane < kScanThreads / 32)
             warp_tot[lane] = w; // inclusive prefix of warp totals
     }
-    __syncthreads();
+    scan_barrier<BAR>();
     const T before = warp > 0 ? warp_tot[warp - 1] : T(0);
     *total = warp_tot[kScanThreads / 32 - 1];
-    __syncthreads(); // warp_tot is reused by the next call
-    return before + (incl - v);
+    scan_barrier<BAR>(); // warp_tot is reused by the next call
+    // The exclusive value is the left neighbour's inclusive one (incl - v
+    // would round, and turn an infinite own value into NaN).
+    const T left = __shfl_up_sync(0xffffffffu, incl, 1);
+    return lane > 0 ? before + left : before;
 }
 
 // Phase 2: carry[c] = sum of partial[0 .. c) (one CTA, fixed order).
@@ -215,9 +235,498 @@ scan_chunks_kernel(const void *__restrict__ src, void *__restrict__ dst, int64_t
     }
 }
 
+// ----------------------------------------------------- single pass
+
+// Carries of the single pass, fixed by the chunk index alone.  Chunk c
+// (4096 elements) publishes its total a_c = B(0, c).  Block (k, m) is the
+// aligned run of chunks [m 32^k, (m+1) 32^k); its sum is defined by a fixed
+// tree over its 32 children,
+//     B(k+1, m) = tree( B(k, 32m), ..., B(k, 32m + 31) )
+// (the lane-0 result of a 5-step XOR butterfly).  Writing c in base 32 with
+// digits d_k, the exclusive carry of chunk c adds, level by level from the
+// top, the complete blocks before c inside its level-(k+1) group:
+//     S_k = tree( B(k, 32 (c >> 5(k+1)) + i) for i < d_k, zeros after ),
+//     carry(c) = ((S_top + S_top-1) + ...) + S_0.
+// Every term and every addition order depend on c alone, so results are
+// bit-identical from run to run whatever the timing.  A chunk never waits on
+// another chunk's carry, only on complete blocks of earlier totals, so there
+// is no serial chain.  Block (k+1, m) is formed by whichever child arrives
+// 32nd (a counter per group): one load of the 32 children by a warp, one
+// reduction, one publish -- so the blocks a carry needs are at most a level
+// or two away from the chunk totals themselves.
+constexpr int kRadixLog = 5;
+constexpr int kMaxLevels = 7; // 2^40 elements = 2^28 chunks -> 7 levels of radix 32
+
+struct ScanLevels {
+    int levels;                     // block levels 0 .. levels-1
+    int64_t count[kMaxLevels];      // blocks at level k: ceil(chunks / 32^k)
+    uint64_t block_off[kMaxLevels]; // first block slot of level k
+    uint64_t group_off[kMaxLevels]; // first group counter of level k (k < levels-1)
+};
+
+// A published block sum is two 64-bit words, each a nonzero tag over one
+// 32-bit half of the value, so a reader that sees both tags has the whole
+// value: no fence orders the halves (the slots start zeroed every launch).
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename C>
+__device__ __forceinline__ void publish_block(unsigned long long *slot, C v)
+{
+    static_assert(sizeof(C) == 8, "64-bit carries");
+    unsigned long long bits;
+    memcpy(&bits, &v, 8);
+    st_relaxed_u64(slot, (1ull << 32) | (bits & 0xffffffffull));
+    st_relaxed_u64(slot + 1, (1ull << 32) | (bits >> 32));
+}
+
+template <typename C>
+__device__ __forceinline__ bool try_block(const unsigned long long *slot, C &v)
+{
+    const unsigned long long a = ld_relaxed_u64(slot), b = ld_relaxed_u64(slot + 1);
+    if ((a >> 32) == 0ull || (b >> 32) == 0ull)
+        return false;
+    const unsigned long long bits = (a & 0xffffffffull) | (b << 32);
+    memcpy(&v, &bits, 8);
+    return true;
+}
+
+// Bounded wait for a block sum; gives up after limit_ns (value 0).
+template <typename C>
+__device__ bool wait_block(const unsigned long long *slot, C &v, uint64_t limit_ns)
+{
+    if (try_block(slot, v))
+        return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    for (uint32_t spin = 1;; ++spin) {
+        if (try_block(slot, v))
+            return true;
+        if ((spin & 63u) == 0u && ptx::globaltimer_ns() - t0 > limit_ns) {
+            v = C(0);
+            return false;
+        }
+    }
+}
+
+// Shared-memory image of the 128-byte swizzle that TMA applies (the 16-byte
+// chunk index within each 128-byte row is XORed with the row index mod 8;
+// buffers are 1024-byte aligned).  Applied to a logical byte offset.
+__device__ __forceinline__ uint32_t swz128(uint32_t b) { return b ^ (((b >> 7) & 7u) << 4); }
+
+template <int DT>
+struct OnePass {
+    using T = ScanTraits<DT>;
+    using Out = typename T::Out;
+    static constexpr int kInBytes = (DT == OPTIGPU_BFLOAT16 || DT == OPTIGPU_FLOAT16) ? 2 : 4;
+    static constexpr int kOutBytes = int(sizeof(Out));
+    static constexpr int kInStage = kSub * kInBytes;   // 16 KiB or 8 KiB
+    static constexpr int kOutStage = kSub * kOutBytes; // 16 KiB or 32 KiB
+    static constexpr int kSmem = 2 * kInStage + kOutStage + 1024;
+    static constexpr int kInRow = 128 / kInBytes;  // elements per 128-byte row
+    static constexpr int kOutRow = 128 / kOutBytes;
+    static constexpr int kMinBlocks = 3; // CTAs per SM the register budget is sized for
+};
+
+// Element bits (the low 16 bits for 2-byte types) -> in-chunk accumulator.
+template <int DT>
+__device__ __forceinline__ typename ScanTraits<DT>::Acc acc_of_bits(uint32_t w)
+{
+    if constexpr (DT == OPTIGPU_INT32)
+        return static_cast<long long>(static_cast<int32_t>(w));
+    else if constexpr (DT == OPTIGPU_FLOAT32)
+        return __uint_as_float(w);
+    else if constexpr (DT == OPTIGPU_BFLOAT16)
+        return __uint_as_float(w << 16);
+    else
+        return __half2float(__ushort_as_half(static_cast<unsigned short>(w & 0xffffu)));
+}
+
+// Single-pass scan.  A persistent grid claims chunks in order through an
+// integer ticket, and every CTA runs a three-stage software pipeline so that
+// no chunk total ever waits for a carry:
+//   iteration k:  thread 0 starts the TMA load of chunk k+1 (128-byte
+//                 swizzle) into the other half of a two-stage buffer and
+//                 claims chunk k+2; the CTA scans chunk k; then, side by
+//                 side, warp 1 publishes the total of chunk k and forms every
+//                 block it completes, while warp 0 gathers the carry of
+//                 chunk k-1; finally chunk k-1 (kept in registers) gets its
+//                 carry and leaves through a swizzled stage and one TMA store.
+// Totals are published as soon as they exist, so no chain forms: a carry is
+// read about one iteration after the totals it needs were published.  The
+// ragged last chunk, or pointers that are not 16-byte aligned, use the same
+// stages with plain coalesced loads and stores.
+template <int DT>
+__global__ void __launch_bounds__(kScanThreads, OnePass<DT>::kMinBlocks)
+scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
+                    const void *__restrict__ src, void *__restrict__ dst, int64_t n, int64_t num_chunks,
+                    int64_t full_chunks, int in_tma, int out_tma, unsigned long long *ticket, unsigned *groups,
+                    unsigned long long *blocks, const __grid_constant__ ScanLevels L, uint64_t wait_limit_ns,
+                    unsigned *err)
+{
+    using P = OnePass<DT>;
+    using T = ScanTraits<DT>;
+    using Acc = typename T::Acc;
+    using Carry = typename T::Carry;
+    using Out = typename T::Out;
+    constexpr int kWords = kPerThread * P::kInBytes / 4; // raw 32-bit words per thread
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ Acc warp_tot[kScanThreads / 32];
+    __shared__ int64_t s_chunk[3];
+    __shared__ Carry s_excl;
+
+    const uint32_t raw_addr = ptx::smem_addr(smem_raw);
+    const uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
+    unsigned char *stage = smem_raw + pad;
+    const uint32_t stage_addr = raw_addr + pad; // in[0] | in[1] | out
+    const uint32_t out_addr = stage_addr + 2 * P::kInStage;
+    unsigned char *out_stage = stage + 2 * P::kInStage;
+    const uint32_t bar0 = ptx::smem_addr(&full_bar[0]);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    bool failed = false;
+
+    if (t == 0) {
+        if (in_tma) {
+            ptx::mbar_init(bar0, 1);
+            ptx::mbar_init(bar0 + 8, 1);
+            ptx::fence_mbar_init();
+            ptx::prefetch_tensormap(&in_map);
+        }
+        if (out_tma)
+            ptx::prefetch_tensormap(&out_map);
+        const int64_t c0 = int64_t(atomicAdd(ticket, 1ull));
+        s_chunk[0] = c0;
+        if (in_tma && c0 < full_chunks) {
+            ptx::mbar_arrive_expect_tx(bar0, P::kInStage);
+            ptx::tma_load_3d(stage_addr, &in_map, 0, 0, int32_t(c0), bar0);
+        }
+        s_chunk[1] = c0 < num_chunks ? int64_t(atomicAdd(ticket, 1ull)) : num_chunks;
+    }
+    __syncthreads();
+
+    uint32_t raw_prev[kWords];
+    Acc before_prev = Acc(0);
+    int64_t prev = -1;  // chunk whose carry is pending (uniform)
+    uint32_t phase = 0; // bit b: parity of the next completion of stage b
+    for (int it = 0;; ++it) {
+        const int buf = it & 1;
+        const int64_t c = s_chunk[it % 3];
+        const bool has_cur = c < num_chunks;
+        if (!has_cur && prev < 0)
+            break;
+        const int64_t base = c * kSub;
+        const uint32_t in_addr = stage_addr + uint32_t(buf) * P::kInStage;
+        unsigned long long claim = 0;
+        uint32_t raw[kWords];
+        Acc before = Acc(0);
+        if (has_cur) {
+            if (in_tma && c < full_chunks) {
+                const bool ok = ptx::mbar_wait_bounded(bar0 + 8u * uint32_t(buf), (phase >> buf) & 1u, wait_limit_ns);
+                phase ^= 1u << buf;
+                if (__syncthreads_or(!ok)) {
+                    // The copy did not arrive in time: give it one more
+                    // bounded wait, report, and stop.
+                    if (t == 0) {
+                        ptx::mbar_wait_bounded(bar0 + 8u * uint32_t(buf), ((phase >> buf) & 1u) ^ 1u, wait_limit_ns);
+                        atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
+                    }
+                    break;
+                }
+            } else {
+                unsigned char *in_ptr = stage + buf * P::kInStage;
+#pragma unroll
+                for (int k = 0; k < kPerThread; ++k) {
+                    const int e = t + k * kScanThreads;
+                    const int64_t i = base + e;
+                    const uint32_t off = swz128(uint32_t(e * P::kInBytes));
+                    if constexpr (P::kInBytes == 4)
+                        *reinterpret_cast<uint32_t *>(in_ptr + off) =
+                            i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
+                    else
+                        *reinterpret_cast<uint16_t *>(in_ptr + off) =
+                            i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
+                }
+                __syncthreads();
+            }
+            if (t == 0) {
+                // Load the chunk claimed last iteration into the other stage
+                // (its previous contents went to registers one iteration
+                // ago) and claim the one after it; the claim is stored only
+                // after the scan, so its round trip overlaps the scan.
+                const int64_t cn = s_chunk[(it + 1) % 3];
+                if (in_tma && cn < full_chunks) {
+                    const uint32_t nb = bar0 + 8u * uint32_t(buf ^ 1);
+                    ptx::mbar_arrive_expect_tx(nb, P::kInStage);
+                    ptx::tma_load_3d(stage_addr + uint32_t(buf ^ 1) * P::kInStage, &in_map, 0, 0, int32_t(cn), nb);
+                }
+                claim = cn < num_chunks ? atomicAdd(ticket, 1ull) : (unsigned long long)num_chunks;
+            }
+            // Thread t scans elements 16 t .. 16 t + 15 of the chunk.
+            const uint32_t region = uint32_t(t) * kPerThread * P::kInBytes;
+#pragma unroll
+            for (int q = 0; q < kWords / 4; ++q) {
+                const uint4 w = ptx::lds_v4(in_addr + swz128(region + 16u * q));
+                raw[4 * q] = w.x;
+                raw[4 * q + 1] = w.y;
+                raw[4 * q + 2] = w.z;
+                raw[4 * q + 3] = w.w;
+            }
+            Acc run = Acc(0);
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) {
+                if constexpr (P::kInBytes == 4) {
+                    run += acc_of_bits<DT>(raw[w]);
+                } else {
+                    run += acc_of_bits<DT>(raw[w] & 0xffffu);
+                    run += acc_of_bits<DT>(raw[w] >> 16);
+                }
+            }
+            Acc total;
+            before = block_exclusive_scan<Acc>(run, warp_tot, &total);
+            if (warp == 1) {
+                // Publish B(0, c), then form every block this chunk completes
+                // as the 32nd arrival of its group.
+                if (lane == 0)
+                    publish_block<Carry>(blocks + 2 * (L.block_off[0] + uint64_t(c)), Carry(total));
+                int64_t j = c;
+                for (int k = 0; k + 1 < L.levels; ++k) {
+                    const int64_t parent = j >> kRadixLog;
+                    if (((parent + 1) << kRadixLog) > L.count[k])
+                        break; // an incomplete group is never needed
+                    unsigned last = 0;
+                    if (lane == 0)
+                        last = atomicAdd(groups + L.group_off[k] + uint64_t(parent), 1u) == 31u;
+                    if (!__shfl_sync(0xffffffffu, last, 0))
+                        break; // later arrivals form it
+                    Carry x;
+                    if (!wait_block<Carry>(blocks + 2 * (L.block_off[k] + uint64_t((parent << kRadixLog) + lane)), x,
+                                           wait_limit_ns))
+                        failed = true;
+#pragma unroll
+                    for (int d = 16; d; d >>= 1)
+                        x += __shfl_xor_sync(0xffffffffu, x, d);
+                    if (lane == 0)
+                        publish_block<Carry>(blocks + 2 * (L.block_off[k + 1] + uint64_t(parent)), x);
+                    j = parent;
+                }
+            }
+        }
+
+        const bool pending = prev >= 0;
+        if (warp == 0) {
+            // Carry of the pending chunk: start every block load, then wait,
+            // reduce each level, add from the top level down.
+            Carry excl = Carry(0);
+            if (prev > 0) {
+                Carry xk[kMaxLevels];
+                unsigned ready = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxLevels; ++k) {
+                    xk[k] = Carry(0);
+                    if (k < L.levels && lane < int((prev >> (kRadixLog * k)) & 31) &&
+                        try_block<Carry>(blocks + 2 * (L.block_off[k] +
+                                                       uint64_t(((prev >> (kRadixLog * (k + 1))) << kRadixLog) + lane)),
+                                         xk[k]))
+                        ready |= 1u << k;
+                }
+                bool first = true;
+#pragma unroll
+                for (int k = kMaxLevels - 1; k >= 0; --k) {
+                    if (k >= L.levels)
+                        continue;
+                    const int d = int((prev >> (kRadixLog * k)) & 31);
+                    if (d == 0)
+                        continue; // uniform across the warp
+                    if (lane < d && !((ready >> k) & 1u) &&
+                        !wait_block<Carry>(blocks + 2 * (L.block_off[k] +
+                                                         uint64_t(((prev >> (kRadixLog * (k + 1))) << kRadixLog) + lane)),
+                                           xk[k], wait_limit_ns))
+                        failed = true;
+                    Carry x = lane < d ? xk[k] : Carry(0);
+#pragma unroll
+                    for (int dd = 16; dd; dd >>= 1)
+                        x += __shfl_xor_sync(0xffffffffu, x, dd);
+                    x = __shfl_sync(0xffffffffu, x, 0);
+                    excl = first ? x : excl + x;
+                    first = false;
+                }
+            }
+            if (t == 0) {
+                s_excl = excl;
+                if (has_cur)
+                    s_chunk[(it + 2) % 3] = int64_t(claim);
+                if (out_tma)
+                    ptx::bulk_wait_group_read<0>(); // the previous store has left the out stage
+            }
+        }
+        __syncthreads();
+
+        if (pending) {
+            // Outputs of the pending chunk: its sequential run again (the
+            // same operations, so the same bits), plus the thread's block
+            // prefix, plus the carry.
+            const typename T::Split sc = T::split(s_excl);
+            Acc v[kPerThread];
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) {
+                if constexpr (P::kInBytes == 4) {
+                    v[w] = acc_of_bits<DT>(raw_prev[w]);
+                } else {
+                    v[2 * w] = acc_of_bits<DT>(raw_prev[w] & 0xffffu);
+                    v[2 * w + 1] = acc_of_bits<DT>(raw_prev[w] >> 16);
+                }
+            }
+#pragma unroll
+            for (int j = 1; j < kPerThread; ++j)
+                v[j] += v[j - 1];
+            const uint32_t oregion = uint32_t(t) * kPerThread * P::kOutBytes;
+            if constexpr (P::kOutBytes == 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 w;
+                    w.x = __float_as_uint(T::finish(sc, before_prev + v[4 * q]));
+                    w.y = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 1]));
+                    w.z = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 2]));
+                    w.w = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 3]));
+                    ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const unsigned long long a =
+                        static_cast<unsigned long long>(T::finish(sc, before_prev + v[2 * q]));
+                    const unsigned long long b2 =
+                        static_cast<unsigned long long>(T::finish(sc, before_prev + v[2 * q + 1]));
+                    ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
+                                make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
+                }
+            }
+            const bool store_tma = out_tma && prev < full_chunks;
+            if (store_tma)
+                ptx::fence_proxy_async_smem();
+            __syncthreads();
+            if (store_tma) {
+                if (t == 0) {
+                    ptx::tma_store_3d(&out_map, 0, 0, int32_t(prev), out_addr);
+                    ptx::bulk_commit_group();
+                }
+            } else {
+                Out *out = static_cast<Out *>(dst);
+                const int64_t pbase = prev * kSub;
+#pragma unroll
+                for (int k = 0; k < kPerThread; ++k) {
+                    const int e = t + k * kScanThreads;
+                    if (pbase + e < n)
+                        out[pbase + e] = *reinterpret_cast<const Out *>(out_stage + swz128(uint32_t(e * P::kOutBytes)));
+                }
+            }
+        }
+        if (!has_cur)
+            break;
+#pragma unroll
+        for (int w = 0; w < kWords; ++w)
+            raw_prev[w] = raw[w];
+        before_prev = before;
+        prev = c;
+    }
+    if (t == 0 && out_tma)
+        ptx::bulk_wait_group<0>();
+    if (failed)
+        atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
+}
+
+std::atomic<int> g_scan_choice{0}; // 0: single pass, 1: three passes
+
+template <int DT>
+optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, cudaStream_t stream)
+{
+    using P = OnePass<DT>;
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const int64_t chunks = (n + kSub - 1) / kSub, full_chunks = n / kSub;
+    ScanLevels L{};
+    L.levels = 1;
+    L.count[0] = chunks;
+    while (L.count[L.levels - 1] > 1) {
+        if (L.levels == kMaxLevels)
+            return fail(OPTIGPU_ERR_INVALID_ARG, "scan: too many chunks for the carry tree");
+        L.count[L.levels] = (L.count[L.levels - 1] + 31) >> kRadixLog;
+        ++L.levels;
+    }
+    uint64_t slots = 0, ngroups = 0;
+    for (int k = 0; k < L.levels; ++k) {
+        L.block_off[k] = slots;
+        slots += uint64_t(L.count[k]);
+        L.group_off[k] = ngroups;
+        if (k + 1 < L.levels)
+            ngroups += uint64_t(L.count[k + 1]);
+    }
+    // [ticket 256 B][group counters][block slots, 16 B each]; all zeroed.
+    const size_t off_groups = 256, off_blocks = (off_groups + 4 * ngroups + 255) / 256 * 256;
+    const size_t bytes = off_blocks + 16 * slots;
+    void *ws = nullptr;
+    if ((st = stream_workspace(stream, bytes, &ws, 3)) != OPTIGPU_OK)
+        return st;
+    char *b = static_cast<char *>(ws);
+    if ((st = check_cuda(cudaMemsetAsync(b, 0, bytes, stream), "scan: reset ticket and carries")) != OPTIGPU_OK)
+        return st;
+
+    CUtensorMap in_map{}, out_map{};
+    const int in_tma = full_chunks > 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+    const int out_tma = full_chunks > 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0;
+    if (in_tma &&
+        (st = encode_tensor_map_3d_swizzled(&in_map, const_cast<void *>(src),
+                                            P::kInBytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                                            P::kInRow, kSub / P::kInRow, uint64_t(full_chunks), 128,
+                                            uint64_t(P::kInStage), P::kInRow, kSub / P::kInRow,
+                                            CU_TENSOR_MAP_SWIZZLE_128B)) != OPTIGPU_OK)
+        return st;
+    if (out_tma &&
+        (st = encode_tensor_map_3d_swizzled(&out_map, dst,
+                                            P::kOutBytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                                              : CU_TENSOR_MAP_DATA_TYPE_UINT64,
+                                            P::kOutRow, kSub / P::kOutRow, uint64_t(full_chunks), 128,
+                                            uint64_t(P::kOutStage), P::kOutRow, kSub / P::kOutRow,
+                                            CU_TENSOR_MAP_SWIZZLE_128B)) != OPTIGPU_OK)
+        return st;
+
+    const void *fn = reinterpret_cast<const void *>(&scan_onepass_kernel<DT>);
+    static std::atomic<bool> attr_set[64];
+    if (dev.device < 0 || dev.device >= 64 || !attr_set[dev.device].load()) {
+        if ((st = check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P::kSmem),
+                             "cudaFuncSetAttribute(scan)")) != OPTIGPU_OK)
+            return st;
+        if (dev.device >= 0 && dev.device < 64)
+            attr_set[dev.device].store(true);
+    }
+    int per_sm = 0;
+    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScanThreads, P::kSmem),
+                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(scan)")) != OPTIGPU_OK)
+        return st;
+    const int64_t grid = std::min<int64_t>(chunks, int64_t(std::max(per_sm, 1)) * dev.num_sms);
+    scan_onepass_kernel<DT><<<unsigned(grid), kScanThreads, P::kSmem, stream>>>(
+        in_map, out_map, src, dst, n, chunks, full_chunks, in_tma, out_tma,
+        reinterpret_cast<unsigned long long *>(b), reinterpret_cast<unsigned *>(b + off_groups),
+        reinterpret_cast<unsigned long long *>(b + off_blocks), L, wait_limit_ns(), dev.status_word);
+    return check_cuda(cudaGetLastError(), "launch scan (single pass)");
+}
+
 template <int DT>
 optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t stream)
 {
+    if (g_scan_choice.load() == 0)
+        return launch_scan_onepass<DT>(src, dst, n, stream);
     using T = ScanTraits<DT>;
     using P = typename std::conditional<DT == OPTIGPU_INT32, long long, double>::type;
     DeviceInfo dev;
@@ -242,6 +751,15 @@ optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t s
 }
 
 } // namespace
+
+int scan_num_configs() { return 2; }
+const char *scan_config_name(int c)
+{
+    return c == 0 ? "scan single pass (dyadic carries)" : c == 1 ? "scan three passes" : nullptr;
+}
+int scan_selected() { return g_scan_choice.load(); }
+void scan_select(int c) { g_scan_choice.store(c); }
+
 } // namespace optigpu
 
 using namespace optigpu;

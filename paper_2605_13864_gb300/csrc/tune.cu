@@ -28,7 +28,8 @@ std::mutex g_tune_mu;
 
 bool op_dtype_ok(int op, int dtype)
 {
-    return op == OPTIGPU_OP_BATCH || ((op == OPTIGPU_OP_TRANSPOSE || op == OPTIGPU_OP_REDUCE) && dtype_valid(dtype));
+    return op == OPTIGPU_OP_BATCH || op == OPTIGPU_OP_SCAN ||
+           ((op == OPTIGPU_OP_TRANSPOSE || op == OPTIGPU_OP_REDUCE) && dtype_valid(dtype));
 }
 
 struct Events {
@@ -105,6 +106,8 @@ int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype)
         return -1;
     if (op == OPTIGPU_OP_BATCH)
         return batch_num_configs();
+    if (op == OPTIGPU_OP_SCAN)
+        return scan_num_configs();
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_num_configs(esize_of(dtype)) : reduce_num_configs();
 }
 
@@ -114,6 +117,8 @@ const char *optigpu_tune_config_name(optigpu_op op, optigpu_dtype dtype, int con
         return nullptr;
     if (op == OPTIGPU_OP_BATCH)
         return batch_config_name(config);
+    if (op == OPTIGPU_OP_SCAN)
+        return scan_config_name(config);
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_config_name(esize_of(dtype), config) : reduce_config_name(config);
 }
 
@@ -125,6 +130,8 @@ optigpu_status optigpu_tune_select(optigpu_op op, optigpu_dtype dtype, int confi
         return fail(OPTIGPU_ERR_INVALID_ARG, "tune: configuration index out of range");
     if (op == OPTIGPU_OP_BATCH)
         batch_select(config);
+    else if (op == OPTIGPU_OP_SCAN)
+        scan_select(config);
     else if (op == OPTIGPU_OP_TRANSPOSE)
         transpose_select(esize_of(dtype), config);
     else
@@ -138,6 +145,8 @@ int optigpu_tune_selected(optigpu_op op, optigpu_dtype dtype)
         return -1;
     if (op == OPTIGPU_OP_BATCH)
         return batch_selected();
+    if (op == OPTIGPU_OP_SCAN)
+        return scan_selected();
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_selected(esize_of(dtype)) : reduce_selected();
 }
 
@@ -164,7 +173,7 @@ int64_t optigpu_tune_get_param(const char *name)
 optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows, int64_t cols, int reps,
                                 optigpu_stream_t stream, int *best_config, float *best_ms)
 {
-    if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH)
+    if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH || op == OPTIGPU_OP_SCAN)
         return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: unknown op or dtype (batches: optigpu_batch_autotune)");
     if (rows <= 0 || cols <= 0 || rows > (int64_t(1) << 31) || cols > (int64_t(1) << 31) || reps < 1 ||
         reps > 1000)
@@ -235,6 +244,7 @@ optigpu_status optigpu_tune_save(const char *path)
     }
     f << "reduce " << reduce_config_name(reduce_selected()) << "\n";
     f << "batch " << batch_config_name(batch_selected()) << "\n";
+    f << "scan " << scan_config_name(scan_selected()) << "\n";
     f << "param transpose.group_rows " << transpose_group_rows() << "\n";
     return f ? OPTIGPU_OK : fail(OPTIGPU_ERR_INVALID_ARG, "tune_save: write failed");
 }
@@ -278,6 +288,14 @@ optigpu_status optigpu_tune_load(const char *path)
             for (int c = 0; c < batch_num_configs(); ++c)
                 if (name == batch_config_name(c)) {
                     batch_select(c);
+                    ++applied;
+                }
+        } else if (kind == "scan") {
+            std::string name;
+            std::getline(in >> std::ws, name);
+            for (int c = 0; c < scan_num_configs(); ++c)
+                if (name == scan_config_name(c)) {
+                    scan_select(c);
                     ++applied;
                 }
         } else if (kind == "param") {

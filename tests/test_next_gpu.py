@@ -113,9 +113,18 @@ def _abs_bits(a, dtype):
     return np.abs(a)
 
 
+@pytest.fixture(params=[0, 1], ids=["single_pass", "three_pass"])
+def scan_config(request):
+    prev = api.tune_selected("scan", torch.float32)
+    api.tune_select("scan", torch.float32, request.param)
+    yield request.param
+    api.tune_select("scan", torch.float32, prev)
+
+
 @pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16", "float16"])
-@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 4095, 4096, 4097, 16384, 16385, 3 * 16384 + 77, 1 << 20])
-def test_scan_matches_oracle(dtype, n):
+@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 4095, 4096, 4097, 16384, 16385, 3 * 16384 + 77, 1 << 20,
+                               (1 << 23) + 11])
+def test_scan_matches_oracle(dtype, n, scan_config):
     a = workloads.vector(n, dtype, seed=n + 3)
     got = api.scan(to_device(a, dtype))
     torch.cuda.synchronize()
@@ -130,7 +139,7 @@ def test_scan_matches_oracle(dtype, n):
         assert (err <= 1e-6 * scale + 1e-30).all(), (n, float(err.max()))
 
 
-def test_scan_closed_form_and_repeatability():
+def test_scan_closed_form_and_repeatability(scan_config):
     n = (1 << 22) + 5
     a = np.arange(n, dtype=np.int64).astype(np.int32) % 1000
     d = to_device(np.ascontiguousarray(a), "int32")
@@ -142,6 +151,55 @@ def test_scan_closed_form_and_repeatability():
     r1 = api.scan(df).cpu().numpy()
     r2 = api.scan(df).cpu().numpy()
     assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))   # bit-identical runs
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16"])
+@pytest.mark.parametrize("n", [5000, 3 * 4096, 70001])
+def test_scan_unaligned_pointers(dtype, n, scan_config):
+    # Source and destination off the 16-byte grid: the single pass takes its
+    # plain-load / plain-store path for every chunk.
+    a = workloads.vector(n, dtype, seed=n + 11)
+    d = to_device(a, dtype, offset_elems=1)
+    odt = torch.int64 if dtype == "int32" else torch.float32
+    out = torch.empty(n + 1, dtype=odt, device="cuda")[1:]
+    api.scan(d, out=out)
+    torch.cuda.synchronize()
+    api.stream_status()
+    want = oracle.scan(a, dtype)
+    g = out.cpu().numpy()
+    if dtype == "int32":
+        assert np.array_equal(g, want)
+    else:
+        scale = oracle.scan(_abs_bits(a, dtype), dtype)
+        assert (np.abs(g.astype(np.float64) - want) <= 1e-6 * scale + 1e-30).all()
+
+
+@pytest.mark.parametrize("n", [4096 * 5 + 3, 1 << 20])
+def test_scan_infinities_and_nan(n, scan_config):
+    # IEEE semantics of the running sum: +inf from the first +inf on, NaN
+    # from the first point where both infinities (or a NaN) are included.
+    a = workloads.vector(n, "float32", seed=n + 21)
+    i1, i2, i3 = n // 7, n // 3, (2 * n) // 3
+    a[i1] = np.float32(np.inf)
+    a[i2 + 1] = np.float32(np.inf)
+    a[i3] = np.float32(-np.inf)
+    got = api.scan(to_device(a, "float32")).cpu().numpy().astype(np.float64)
+    want = oracle.scan(a, "float32")
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(np.isposinf(got), np.isposinf(want))
+    fin = np.isfinite(want)
+    assert np.isfinite(got[fin]).all()
+    scale = oracle.scan(np.abs(np.where(np.isfinite(a), a, 0)).astype(np.float32), "float32")
+    assert (np.abs(got[fin] - want[fin]) <= 1e-6 * scale[fin] + 1e-30).all()
+
+
+def test_scan_repeatable_many_chunks(scan_config):
+    # 2^24 fp32 = 4096 single-pass chunks: bit-identical over repeated runs.
+    f = workloads.vector(1 << 24, "float32", seed=9)
+    df = to_device(f, "float32")
+    first = api.scan(df).cpu().numpy().view(np.uint32)
+    for _ in range(3):
+        assert np.array_equal(api.scan(df).cpu().numpy().view(np.uint32), first)
 
 
 @pytest.mark.parametrize("lo,width,nbins", [(0, 1, 100), (-50, 7, 29), (-1000, 1, 2001), (0, 16, 4096),
