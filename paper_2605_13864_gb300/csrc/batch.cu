@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -31,6 +32,7 @@ namespace optigpu {
 namespace {
 
 constexpr int kBatchThreads = 256;
+static_assert(sizeof(BatchInst) % 8 == 0 && alignof(BatchInst) >= 8, "descriptors are copied in 8-byte words");
 
 // Largest shared tile, in 32-bit words, for tiles of `AREA` elements: the row
 // pitch S is TW + 1 words (TW + 2 halves for 16-bit data), so TH * S is at
@@ -47,10 +49,24 @@ struct BatchShared {
         ReduceCore<OPTIGPU_FLOAT16, false>::Shared rh;
         ReduceCore<OPTIGPU_FLOAT16, true>::Shared rhc;
     } u;
-    BatchInst desc[2];
-    int64_t item[2];
+    // Ring of the next items: slot i & 3 holds this CTA's i-th item, its
+    // instance index and its descriptor (filled one to three items ahead).
+    BatchInst desc[4];
+    int64_t item[4];
+    uint32_t iidx[4];
     int last;
 };
+
+// Asynchronous copies global -> shared (L1-cached: the tables are read-only)
+// and their completion, for the descriptor prefetch.
+__device__ __forceinline__ void cp_async_4(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))), "l"(gsrc) : "memory");
+}
 
 // Row pitch of the shared tile in elements.  Reading a tile column means
 // consecutive lanes step by one pitch; an odd pitch in 32-bit words puts them
@@ -112,6 +128,14 @@ __device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local,
     auto &rs = *reinterpret_cast<typename Core::Shared *>(&sh);
     P *mine = static_cast<P *>(partials) + in.aux;
     const P part = Core::chunk_partial(in.src, in.rows, local, in.vec_ok != 0, rs);
+    if (in.nitems == 1) {
+        // A one-chunk sum: the fixed-order combine of a single partial is
+        // 0 + partial (the other lanes add zeros), written without the
+        // partials array, the fence and the completion counter.
+        if (threadIdx.x == 0)
+            *static_cast<P *>(in.dst) = P(0) + part;
+        return;
+    }
     if (threadIdx.x == 0) {
         mine[local] = part;
         __threadfence();
@@ -126,29 +150,53 @@ __device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local,
     }
 }
 
+// Persistent batch kernel.  Items come from one integer atomic queue in a
+// three-stage prefetch, so no round trip sits between two items: while item
+// i runs, thread 0 claims item i+3, and warp 0 copies item i+2's instance
+// index and item i+1's descriptor into the shared ring (cp.async), all
+// completed by the barrier that ends item i.
 template <int AREA>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, 4)
 batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ item_inst, int64_t total_items,
              unsigned long long *queue, unsigned *inst_done, void *partials, int compensated)
 {
     __shared__ BatchShared<AREA> sh;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     if (t == 0) {
-        const int64_t it = int64_t(atomicAdd(queue, 1ull));
-        sh.item[0] = it;
-        if (it < total_items)
-            sh.desc[0] = insts[item_inst[it]];
+        int64_t prev = 0;
+        for (int k = 0; k < 3; ++k) {
+            const int64_t it = (k == 0 || prev < total_items) ? int64_t(atomicAdd(queue, 1ull)) : total_items;
+            sh.item[k] = it;
+            prev = it;
+        }
+        sh.item[3] = total_items;
+        if (sh.item[0] < total_items) {
+            sh.iidx[0] = item_inst[sh.item[0]];
+            sh.desc[0] = insts[sh.iidx[0]];
+        }
+        if (sh.item[1] < total_items)
+            sh.iidx[1] = item_inst[sh.item[1]];
     }
     __syncthreads();
-    for (int cur = 0;; cur ^= 1) {
+    for (int i = 0;; ++i) {
+        const int cur = i & 3;
         const int64_t item = sh.item[cur];
         if (item >= total_items)
             break;
-        int64_t next = 0;
-        if (t == 0)
-            next = int64_t(atomicAdd(queue, 1ull)); // claim ahead, used after this item
+        int64_t next = total_items;
+        if (t < 32) {
+            const int64_t i2 = sh.item[(i + 2) & 3], i1 = sh.item[(i + 1) & 3];
+            if (t == 0 && i2 < total_items)
+                next = int64_t(atomicAdd(queue, 1ull)); // item i+3, stored after this item
+            if (lane == 0 && i2 < total_items)
+                cp_async_4(&sh.iidx[(i + 2) & 3], item_inst + i2);
+            if (i1 < total_items && lane < int(sizeof(BatchInst) / 8))
+                cp_async_8(reinterpret_cast<char *>(&sh.desc[(i + 1) & 3]) + 8 * lane,
+                           reinterpret_cast<const char *>(insts + sh.iidx[(i + 1) & 3]) + 8 * lane);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
         const BatchInst in = sh.desc[cur];
-        const uint32_t inst = item_inst[item];
+        const uint32_t inst = sh.iidx[cur];
         const int64_t local = item - in.first_item;
         if (in.op == OPTIGPU_OP_TRANSPOSE) {
             if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
@@ -181,12 +229,12 @@ batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ i
                 break;
             }
         }
-        if (t == 0) {
-            sh.item[cur ^ 1] = next;
-            if (next < total_items)
-                sh.desc[cur ^ 1] = insts[item_inst[next]];
+        if (t < 32) {
+            if (t == 0)
+                sh.item[(i + 3) & 3] = next;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        __syncthreads(); // publishes the next item; the tile / reduce scratch may be reused
+        __syncthreads(); // publishes the prefetched entries; the tile / reduce scratch may be reused
     }
 }
 
@@ -652,6 +700,59 @@ void optigpu_batch_plan_destroy(optigpu_batch_plan *plan)
 
 // ------------------------------------------------------------ segmented sums
 
+namespace optigpu {
+namespace {
+
+// Pinned staging for the per-call tables of optigpu_reduce_segmented: two
+// page-locked buffers per (device, stream), each reused only after the copy
+// made from it has run (its event), so the upload is a true asynchronous
+// copy that never waits for the stream's earlier work.  Held until exit.
+struct SegStage {
+    void *host[2] = {nullptr, nullptr};
+    size_t cap[2] = {0, 0};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    unsigned next = 0;
+};
+std::mutex g_seg_mu;
+std::map<std::pair<int, cudaStream_t>, SegStage> g_seg_stage;
+
+optigpu_status seg_stage_buffer(cudaStream_t s, size_t bytes, void **buf, cudaEvent_t *ev)
+{
+    int dev = -1;
+    optigpu_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != OPTIGPU_OK)
+        return st;
+    std::lock_guard<std::mutex> lk(g_seg_mu);
+    SegStage &g = g_seg_stage[std::make_pair(dev, s)];
+    const unsigned b = g.next++ & 1u;
+    if (g.done[b]) {
+        if ((st = check_cuda(cudaEventSynchronize(g.done[b]), "reduce_segmented: staging reuse")) != OPTIGPU_OK)
+            return st;
+    } else if ((st = check_cuda(cudaEventCreateWithFlags(&g.done[b], cudaEventDisableTiming),
+                                "reduce_segmented: staging event")) != OPTIGPU_OK) {
+        return st;
+    }
+    if (g.cap[b] < bytes) {
+        if (g.host[b])
+            cudaFreeHost(g.host[b]);
+        g.host[b] = nullptr;
+        g.cap[b] = 0;
+        const size_t want = std::max<size_t>(bytes, size_t(1) << 16);
+        if (cudaHostAlloc(&g.host[b], want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            g.host[b] = nullptr;
+            return fail(OPTIGPU_ERR_OOM, "reduce_segmented: pinned staging allocation failed");
+        }
+        g.cap[b] = want;
+    }
+    *buf = g.host[b];
+    *ev = g.done[b];
+    return OPTIGPU_OK;
+}
+
+} // namespace
+} // namespace optigpu
+
 extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets, int32_t nseg,
                                                    optigpu_dtype dtype, void *out, uint32_t flags,
                                                    optigpu_stream_t stream)
@@ -700,14 +801,21 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
     void *ws = nullptr;
     if ((st = stream_workspace(s, L.total, &ws, 1)) != OPTIGPU_OK)
         return st;
-    // One host image of [instances | item map], copied in one call (pageable
-    // source: the copy is staged before cudaMemcpyAsync returns).
-    std::vector<char> image(L.off_part - L.off_inst);
-    std::memcpy(image.data(), t.insts.data(), sizeof(BatchInst) * t.insts.size());
-    std::memcpy(image.data() + (L.off_items - L.off_inst), t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size());
+    // One image of [instances | item map] in pinned memory, copied in one
+    // asynchronous call.
+    const size_t image_bytes = L.off_part - L.off_inst;
+    void *image = nullptr;
+    cudaEvent_t copied = nullptr;
+    if ((st = seg_stage_buffer(s, image_bytes, &image, &copied)) != OPTIGPU_OK)
+        return st;
+    std::memcpy(image, t.insts.data(), sizeof(BatchInst) * t.insts.size());
+    std::memcpy(static_cast<char *>(image) + (L.off_items - L.off_inst), t.item_inst.data(),
+                sizeof(uint32_t) * t.item_inst.size());
     char *base = static_cast<char *>(ws);
-    if ((st = check_cuda(cudaMemcpyAsync(base + L.off_inst, image.data(), image.size(), cudaMemcpyHostToDevice, s),
+    if ((st = check_cuda(cudaMemcpyAsync(base + L.off_inst, image, image_bytes, cudaMemcpyHostToDevice, s),
                          "reduce_segmented: upload tables")) != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaEventRecord(copied, s), "reduce_segmented: staging event")) != OPTIGPU_OK)
         return st;
     return batch_launch(config, reinterpret_cast<BatchInst *>(base + L.off_inst),
                         reinterpret_cast<uint32_t *>(base + L.off_items), t.items,

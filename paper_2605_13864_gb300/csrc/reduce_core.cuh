@@ -253,11 +253,25 @@ struct ReduceCore {
                     acc.add(T::vec_sum(buf[u]));
             }
         } else {
-            for (int k = 0; k < VPT; ++k) {
-                const int64_t first = base + int64_t(k * kReduceThreads + t) * V;
-                if (first >= n)
-                    break; // the rest of this thread's vectors are all past n: zeros
-                acc.add(T::vec_sum(gather_vector<DT>(src, n, first)));
+            // Ragged or unaligned chunk: the same vectors in the same order,
+            // gathered from scalar reads.  A batch's reads are all issued
+            // before any is added, so they are in flight together; vectors
+            // that start at or past n are not added (as in the full path,
+            // where none exist).
+#pragma unroll
+            for (int k0 = 0; k0 < VPT; k0 += BATCH) {
+                uint4 buf[BATCH];
+#pragma unroll
+                for (int u = 0; u < BATCH; ++u) {
+                    const int64_t first = base + int64_t((k0 + u) * kReduceThreads + t) * V;
+                    buf[u] = first < n ? gather_vector<DT>(src, n, first) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < BATCH; ++u) {
+                    const int64_t first = base + int64_t((k0 + u) * kReduceThreads + t) * V;
+                    if (first < n)
+                        acc.add(T::vec_sum(buf[u]));
+                }
             }
         }
         return to_partial(block_combine(acc, sh));
