@@ -357,8 +357,8 @@ optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, 
 }
 
 optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
-                            unsigned long long *d_queue, unsigned *d_done, void *d_partials, int compensated,
-                            cudaStream_t stream, int *grid_out)
+                            unsigned long long *d_queue, unsigned *d_done, int64_t clear_done, void *d_partials,
+                            int compensated, cudaStream_t stream, int *grid_out)
 {
     const BatchConfig &c = batch_configs()[size_t(config)];
     DeviceInfo dev;
@@ -373,8 +373,12 @@ optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t
     if (c.ctas_per_sm > 0)
         per_sm = std::min(per_sm, c.ctas_per_sm);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(per_sm) * dev.num_sms));
-    if ((st = check_cuda(cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), stream),
-                         "batch: reset queue")) != OPTIGPU_OK)
+    // The counters follow the queue in the layout (batch_layout), so one
+    // memset covers both when they must be cleared.
+    const size_t clear = clear_done > 0 ? size_t(reinterpret_cast<char *>(d_done + clear_done) -
+                                                 reinterpret_cast<char *>(d_queue))
+                                        : sizeof(unsigned long long);
+    if ((st = check_cuda(cudaMemsetAsync(d_queue, 0, clear, stream), "batch: reset queue")) != OPTIGPU_OK)
         return st;
     int comp = compensated;
     void *args[] = {&d_insts, &d_item_inst, &items, &d_queue, &d_done, &d_partials, &comp};
@@ -469,7 +473,7 @@ void free_plan_device(optigpu_batch_plan *p)
 // on `stream`.
 optigpu_status enqueue_run(optigpu_batch_plan *p, int config, cudaStream_t stream, int *grid_out)
 {
-    return batch_launch(config, p->d_insts, p->d_item_inst, p->total_items, p->d_queue, p->d_inst_done,
+    return batch_launch(config, p->d_insts, p->d_item_inst, p->total_items, p->d_queue, p->d_inst_done, 0,
                         p->d_partials, (p->flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, stream, grid_out);
 }
 
@@ -770,47 +774,65 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: out must be 8-byte aligned");
     if (offsets[0] < 0)
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: negative offset");
-    for (int32_t s = 0; s < nseg; ++s)
-        if (offsets[s + 1] < offsets[s] || offsets[s + 1] > (int64_t(1) << 40))
+    // One pass validates and counts: instances are the non-empty segments,
+    // items their 16384-element chunks.
+    int64_t ninst = 0, items = 0;
+    for (int32_t k = 0; k < nseg; ++k) {
+        const int64_t len = offsets[k + 1] - offsets[k];
+        if (len < 0 || offsets[k + 1] > (int64_t(1) << 40))
             return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: offsets must be non-decreasing and < 2^40");
+        if (len > 0) {
+            ++ninst;
+            items += (len + kReduceChunk - 1) / kReduceChunk;
+        }
+    }
     const size_t es = esize_of(dtype);
     if (offsets[nseg] > offsets[0] && (!src || reinterpret_cast<uintptr_t>(src) % es))
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: src must be non-null and element-aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    std::vector<optigpu_desc> descs(static_cast<size_t>(nseg));
-    for (int32_t k = 0; k < nseg; ++k) {
-        optigpu_desc &d = descs[size_t(k)];
-        d.op = OPTIGPU_OP_REDUCE;
-        d.dtype = int32_t(dtype);
-        d.src = static_cast<const char *>(src) + offsets[k] * int64_t(es);
-        d.dst = static_cast<char *>(out) + 8 * size_t(k);
-        d.rows = offsets[k + 1] - offsets[k];
-        d.cols = 1;
-    }
     // Empty segments have no chunk: clear every result first.
     optigpu_status st = check_cuda(cudaMemsetAsync(out, 0, 8 * size_t(nseg), s), "reduce_segmented: clear out");
-    if (st != OPTIGPU_OK)
+    if (st != OPTIGPU_OK || items == 0)
         return st;
-    BatchTables t;
     const int config = 0;
-    if ((st = batch_tables(descs.data(), nseg, batch_tile(config), t)) != OPTIGPU_OK)
-        return st;
-    if (t.items == 0)
-        return OPTIGPU_OK;
-    const BatchLayout L = batch_layout(nseg, t.items, t.chunks);
+    const BatchLayout L = batch_layout(ninst, items, items);
     void *ws = nullptr;
     if ((st = stream_workspace(s, L.total, &ws, 1)) != OPTIGPU_OK)
         return st;
-    // One image of [instances | item map] in pinned memory, copied in one
-    // asynchronous call.
+    // The second pass writes [instances | item map] straight into pinned
+    // memory, copied in one asynchronous call.
     const size_t image_bytes = L.off_part - L.off_inst;
     void *image = nullptr;
     cudaEvent_t copied = nullptr;
     if ((st = seg_stage_buffer(s, image_bytes, &image, &copied)) != OPTIGPU_OK)
         return st;
-    std::memcpy(image, t.insts.data(), sizeof(BatchInst) * t.insts.size());
-    std::memcpy(static_cast<char *>(image) + (L.off_items - L.off_inst), t.item_inst.data(),
-                sizeof(uint32_t) * t.item_inst.size());
+    BatchInst *bi = static_cast<BatchInst *>(image);
+    uint32_t *map = reinterpret_cast<uint32_t *>(static_cast<char *>(image) + (L.off_items - L.off_inst));
+    uint32_t k_inst = 0;
+    int64_t it = 0;
+    for (int32_t k = 0; k < nseg; ++k) {
+        const int64_t len = offsets[k + 1] - offsets[k];
+        if (len == 0)
+            continue;
+        BatchInst b;
+        std::memset(&b, 0, sizeof b);
+        b.src = static_cast<const char *>(src) + offsets[k] * int64_t(es);
+        b.dst = static_cast<char *>(out) + 8 * size_t(k);
+        b.rows = len;
+        b.cols = 1;
+        b.first_item = it;
+        b.aux = it; // one partial per chunk, in item order
+        b.op = OPTIGPU_OP_REDUCE;
+        b.dtype = int32_t(dtype);
+        const int64_t nit = (len + kReduceChunk - 1) / kReduceChunk;
+        b.nitems = int32_t(nit);
+        b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
+        bi[k_inst] = b;
+        for (int64_t j = 0; j < nit; ++j)
+            map[it + j] = k_inst;
+        it += nit;
+        ++k_inst;
+    }
     char *base = static_cast<char *>(ws);
     if ((st = check_cuda(cudaMemcpyAsync(base + L.off_inst, image, image_bytes, cudaMemcpyHostToDevice, s),
                          "reduce_segmented: upload tables")) != OPTIGPU_OK)
@@ -818,8 +840,8 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
     if ((st = check_cuda(cudaEventRecord(copied, s), "reduce_segmented: staging event")) != OPTIGPU_OK)
         return st;
     return batch_launch(config, reinterpret_cast<BatchInst *>(base + L.off_inst),
-                        reinterpret_cast<uint32_t *>(base + L.off_items), t.items,
+                        reinterpret_cast<uint32_t *>(base + L.off_items), items,
                         reinterpret_cast<unsigned long long *>(base + L.off_queue),
-                        reinterpret_cast<unsigned *>(base + L.off_done), base + L.off_part,
+                        reinterpret_cast<unsigned *>(base + L.off_done), ninst, base + L.off_part,
                         (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr);
 }

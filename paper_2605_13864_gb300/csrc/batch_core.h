@@ -63,8 +63,12 @@ optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, 
 int batch_tile(int config);
 
 // Enqueues the queue reset and the persistent batch kernel on `stream`.
+// `clear_done` instances' completion counters are zeroed too (with the queue,
+// which the layout places right before them): callers whose workspace held
+// other tables before pass their instance count; plans, whose counters start
+// at zero and are left at zero by every run, pass 0.
 optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
-                            unsigned long long *d_queue, unsigned *d_done, void *d_partials, int compensated,
-                            cudaStream_t stream, int *grid_out);
+                            unsigned long long *d_queue, unsigned *d_done, int64_t clear_done, void *d_partials,
+                            int compensated, cudaStream_t stream, int *grid_out);
 
 } // namespace optigpu

@@ -389,8 +389,8 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
             if ((st = batch_launch(config, reinterpret_cast<BatchInst *>(ws + L.off_inst),
                                    reinterpret_cast<uint32_t *>(ws + L.off_items), t.items,
                                    reinterpret_cast<unsigned long long *>(ws + L.off_queue),
-                                   reinterpret_cast<unsigned *>(ws + L.off_done), ws + L.off_part,
-                                   rflags ? 1 : 0, sc.s, nullptr)) != OPTIGPU_OK)
+                                   reinterpret_cast<unsigned *>(ws + L.off_done), int64_t(descs.size()),
+                                   ws + L.off_part, rflags ? 1 : 0, sc.s, nullptr)) != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
         }

@@ -93,6 +93,25 @@ def test_reduce_segmented_many_small_segments():
     assert got.tolist() == oracle.segmented_sums(a, offs)
 
 
+def test_reduce_segmented_back_to_back_calls():
+    # Several one-shot calls queued on one stream without a sync in between:
+    # each call's tables go through the pinned staging pair, which must not
+    # be overwritten before its copy has run.
+    rng = np.random.default_rng(55)
+    a = workloads.vector(3 << 20, "int32", seed=56)
+    d = to_device(a, "int32")
+    cases = []
+    for _ in range(6):
+        lens = rng.integers(0, 40000, size=int(rng.integers(1, 200)))
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        offs = np.minimum(offs, a.size)
+        cases.append((offs, api.reduce_segmented(d, offs)))
+    torch.cuda.synchronize()
+    api.stream_status()
+    for offs, got in cases:
+        assert got.cpu().numpy().tolist() == oracle.segmented_sums(a, offs)
+
+
 @pytest.mark.parametrize("dtype", ["float32", "bfloat16", "int32"])
 @pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128, 200, 1000, 4100])
 def test_transpose_inplace(dtype, n):

@@ -105,6 +105,24 @@ def test_served_results_equal_oracle_and_single_calls(per_call, compensated):
     sv.close()
 
 
+def test_growing_steps_reuse_the_step_workspace():
+    """One stream serves a small step of multi-chunk sums, then larger ones:
+    the step workspace is reused with a different table layout each time, so
+    the completion counters must start at zero in every step."""
+    I = workloads.Instance
+    sv = api.Server(budget_bytes=512 << 20, max_slots=256, n_streams=1)
+    for step, count in enumerate((3, 40, 120)):
+        inst = [I(1, "int32", 16384 * 2 + 7 * k + step, 1) for k in range(count)]
+        data = workloads.batched_data(inst, seed=60 + step)
+        reqs = [make_request(i, a) for i, a in zip(inst, data)]
+        for op, src, dst in reqs:
+            sv.submit(op, src, dst)
+        sv.drain()
+        for i, a, (op, src, dst) in zip(inst, data, reqs):
+            assert dst.item() == oracle.sum_i64(a), (step, i)
+    sv.close()
+
+
 def test_pageable_and_pinned_requests_mixed():
     """Pinned requests go through the step's copy kernels, pageable ones
     through copy-engine calls; both give the oracle's results."""
