@@ -687,6 +687,38 @@ def run_case(args):
             plan.run()
         torch.cuda.synchronize()
         plan.close()
+    elif case in ("scan_f32", "scan_i32", "scan3_f32", "scan3_i32"):
+        n = side * side
+        if case.endswith("f32"):
+            v = torch.randn(n, device="cuda")
+            o = torch.empty(n, device="cuda")
+        else:
+            v = torch.randint(0, 4096, (n,), dtype=torch.int32, device="cuda")
+            o = torch.empty(n, dtype=torch.int64, device="cuda")
+        api.tune_select("scan", torch.float32, 1 if case.startswith("scan3") else 0)
+        for _ in range(args.case_reps):
+            api.scan(v, out=o)
+    elif case == "histogram":
+        v = torch.randint(0, 4096, (side * side,), dtype=torch.int32, device="cuda")
+        for _ in range(args.case_reps):
+            api.histogram(v, 0, 1, 4096)
+    elif case == "inplace_f32":
+        m = torch.randn(side, side, device="cuda")
+        for _ in range(args.case_reps):
+            api.transpose_inplace(m)
+    elif case == "transpose_batched_f32":
+        b = max(1, (side * side) // (2048 * 2048))
+        x = torch.randn(b, 2048, 2048, device="cuda")
+        y = torch.empty(b, 2048, 2048, device="cuda")
+        for _ in range(args.case_reps):
+            api.transpose_batched(x, out=y)
+    elif case == "segmented_f32":
+        n = side * side
+        v = torch.randn(n, device="cuda")
+        lens = np.random.default_rng(6).integers(1, 32768, size=max(1, n // 16384))
+        offs = np.minimum(np.concatenate([[0], np.cumsum(lens)]), n)
+        for _ in range(args.case_reps):
+            api.reduce_segmented(v, offs)
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()
@@ -709,7 +741,9 @@ def main():
     ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
-                         "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch)")
+                         "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, "
+                         "scan_f32, scan_i32, scan3_f32, scan3_i32, histogram, inplace_f32, "
+                         "transpose_batched_f32, segmented_f32)")
     ap.add_argument("--side", type=int, default=8192)
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--case-reps", type=int, default=3)

@@ -4,7 +4,8 @@
 //
 // Each CTA of a persistent grid keeps its own copy of the histogram in shared
 // memory (32-bit counters, shared-memory atomics), walks the input with
-// 16-byte loads (grid-stride), and finally adds its non-zero counters into
+// 16-byte loads (grid-stride, four in flight per thread), and finally adds
+// its non-zero counters into
 // the int64 result with one global integer atomic each.  Counting is exact
 // whatever the order, so the result is bit-exact.  Histograms with more bins
 // than fit in shared memory count directly with global atomics.
@@ -58,15 +59,31 @@ histogram_kernel(const int32_t *__restrict__ src, int64_t n, BinRule rule, unsig
     if (vec_ok) {
         const int64_t nv = n / 4;
         const int4 *v = reinterpret_cast<const int4 *>(src);
-        for (int64_t i = tid; i < nv; i += stride) {
+        // kUnroll 16-byte loads per thread in flight before any is counted.
+        constexpr int kUnroll = 4;
+        int64_t i = tid;
+        for (; i + (kUnroll - 1) * stride < nv; i += kUnroll * stride) {
+            int4 q[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                q[u] = __ldcs(v + i + u * stride);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                count(q[u].x);
+                count(q[u].y);
+                count(q[u].z);
+                count(q[u].w);
+            }
+        }
+        for (; i < nv; i += stride) {
             const int4 q = __ldcs(v + i);
             count(q.x);
             count(q.y);
             count(q.z);
             count(q.w);
         }
-        for (int64_t i = nv * 4 + tid; i < n; i += stride)
-            count(src[i]);
+        for (int64_t j = nv * 4 + tid; j < n; j += stride)
+            count(src[j]);
     } else {
         for (int64_t i = tid; i < n; i += stride)
             count(src[i]);

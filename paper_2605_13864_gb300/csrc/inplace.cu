@@ -215,8 +215,12 @@ InplaceConfig make_inplace()
 
 const InplaceConfig &inplace_config(size_t esize)
 {
-    static const InplaceConfig c4 = make_inplace<4, 64, 2, 2>();
-    static const InplaceConfig c2 = make_inplace<2, 64, 4, 2>();
+    // One stage and one output buffer per CTA (64 KiB for fp32, 32 KiB for
+    // 16-bit types): several CTAs per SM keep more pairs in flight than one
+    // deeper pipeline per SM (16384^2: fp32 0.396 -> 0.354 ms, bf16 0.213 ->
+    // 0.191 ms).
+    static const InplaceConfig c4 = make_inplace<4, 64, 1, 1>();
+    static const InplaceConfig c2 = make_inplace<2, 64, 1, 1>();
     return esize == 4 ? c4 : c2;
 }
 
