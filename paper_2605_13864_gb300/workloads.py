@@ -182,6 +182,18 @@ def batched_data(instances, seed: int = 3):
     return data
 
 
+def segment_offsets(n: int, nseg: int, seed: int = 6, max_len: int = 32768) -> np.ndarray:
+    """nseg + 1 offsets of consecutive segments of a length-n array: lengths
+    uniform in [1, max_len), clipped at n (trailing segments may be empty)."""
+    lens = np.random.default_rng(seed).integers(1, max_len, size=nseg)
+    return np.minimum(np.concatenate([[0], np.cumsum(lens)]), n).astype(np.int64)
+
+
+def histogram_values(n: int, nbins: int = 4096, seed: int = 7) -> np.ndarray:
+    """int32 values uniform in [0, nbins)."""
+    return draw(np.random.default_rng(seed), (n,), "int32", "uniform_int", lo=0, hi=nbins - 1)
+
+
 @dataclass
 class Request:
     arrival_s: float

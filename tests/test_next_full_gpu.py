@@ -1,0 +1,99 @@
+"""GPU parity of the neighbouring problems at the benchmark's full sizes.
+
+Each case runs the CUDA path on seeded synthetic inputs of the size the
+benchmark times, and compares with the CPU oracle:
+- the stack of 64 2048 x 2048 float32 transposes: three whole matrices bit-exact,
+  plus 2^20 sampled elements spread over every matrix;
+- the in-place 16384 x 16384 float32 transpose: bit-exact in full;
+- 2^28 float32 in 16384 segments: every segment sum within 1e-6 of the segment's
+  sum of |x|, and sampled segments bit-identical to their single calls;
+- the 2^28-element inclusive scans: every element of int32 -> int64 exact,
+  float32 within 1e-6 of the running sum of |x|;
+- the 2^28-value histogram in 4096 bins: exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import require_gpu, to_device, torch
+from paper_2605_13864_gb300 import api, workloads
+
+pytestmark = pytest.mark.gpu
+N28 = 1 << 28
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    yield
+    torch.cuda.empty_cache()
+
+
+def test_transpose_stack_64x2048x2048():
+    b, r, c = 64, 2048, 2048
+    a = workloads.matrix(b * r, c, "float32", seed=71).reshape(b, r, c)
+    d = to_device(a.reshape(b * r, c), "float32").view(b, r, c)
+    out = api.transpose_batched(d)
+    torch.cuda.synchronize()
+    api.stream_status()
+    del d
+    got = out.cpu().numpy()
+    del out
+    for k in (0, 31, 63):
+        assert np.array_equal(got[k].view(np.uint32), oracle.transpose(a[k]).view(np.uint32)), k
+    rng = np.random.default_rng(72)
+    bi, ri, ci = rng.integers(0, b, 1 << 20), rng.integers(0, r, 1 << 20), rng.integers(0, c, 1 << 20)
+    assert np.array_equal(got[bi, ci, ri].view(np.uint32), a[bi, ri, ci].view(np.uint32))
+
+
+def test_transpose_inplace_16384_float32():
+    n = 16384
+    a = workloads.roofline_matrix(n, n)
+    d = to_device(a, "float32")
+    api.transpose_inplace(d)
+    torch.cuda.synchronize()
+    api.stream_status()
+    got = d.cpu().numpy()
+    del d
+    assert np.array_equal(got.view(np.uint32), oracle.transpose(a).view(np.uint32))
+
+
+def test_segmented_2p28_float32_16384_segments():
+    a = workloads.roofline_vector(N28)
+    offs = workloads.segment_offsets(N28, 16384)
+    d = to_device(a, "float32")
+    got = api.reduce_segmented(d, offs).cpu().numpy()
+    want = oracle.segmented_sums(a, offs, "float32")
+    absums = oracle.segmented_sums(np.abs(a), offs, "float32")
+    for s in range(len(offs) - 1):
+        assert abs(float(got[s]) - want[s]) <= 1e-6 * absums[s] + 1e-300, s
+    for s in np.random.default_rng(73).integers(0, len(offs) - 1, 16):
+        lo, hi = int(offs[s]), int(offs[s + 1])
+        if hi > lo:
+            assert api.reduce_sum(d[lo:hi]).item() == got[s], s
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float32"])
+def test_scan_2p28(dtype):
+    a = workloads.roofline_vector(N28) if dtype == "float32" else workloads.histogram_values(N28, 1 << 20)
+    d = to_device(a, dtype)
+    got = api.scan(d)
+    torch.cuda.synchronize()
+    api.stream_status()
+    del d
+    g = got.cpu().numpy()
+    del got
+    want = oracle.scan(a, dtype)
+    if dtype == "int32":
+        assert np.array_equal(g, want)
+    else:
+        scale = oracle.scan(np.abs(a), dtype)
+        assert (np.abs(g.astype(np.float64) - want) <= 1e-6 * scale + 1e-30).all()
+
+
+def test_histogram_2p28_4096_bins():
+    a = workloads.histogram_values(N28, 4096)
+    got = api.histogram(to_device(a, "int32"), 0, 1, 4096).cpu().numpy()
+    want = oracle.histogram_i32(a, 0, 1, 4096)
+    assert np.array_equal(got, want)
+    assert got.sum() == N28
