@@ -754,6 +754,52 @@ optigpu_status seg_stage_buffer(cudaStream_t s, size_t bytes, void **buf, cudaEv
     return OPTIGPU_OK;
 }
 
+// Instance table of a segmented sum, one thread per segment: segment s is
+// instance s, its items (16384-element chunks) start at first[s], and an
+// empty segment gets no item and a zero result.
+__global__ void seg_instances_kernel(const char *src, int64_t esize, int dtype, char *out, const int64_t *offsets,
+                                     const int64_t *first, int32_t nseg, BatchInst *insts)
+{
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= nseg)
+        return;
+    const int64_t len = offsets[k + 1] - offsets[k];
+    BatchInst b;
+    b.src = src + offsets[k] * esize;
+    b.dst = out + 8 * k;
+    b.rows = len;
+    b.cols = 1;
+    b.first_item = first[k];
+    b.aux = first[k]; // one partial per chunk, in item order
+    b.op = OPTIGPU_OP_REDUCE;
+    b.dtype = dtype;
+    b.nitems = int32_t((len + kReduceChunk - 1) / kReduceChunk);
+    b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
+    b.th_log2 = 0;
+    b.tw_log2 = 0;
+    insts[k] = b;
+    if (len == 0)
+        *reinterpret_cast<long long *>(out + 8 * k) = 0; // the same bits as int64 0 and double +0.0
+}
+
+// Item -> instance map, one thread per item: the segment whose items
+// [first[s], first[s + 1]) contain it (binary search over first[]).
+__global__ void seg_items_kernel(const int64_t *first, int32_t nseg, int64_t items, uint32_t *item_inst)
+{
+    const int64_t it = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (it >= items)
+        return;
+    int32_t lo = 0, hi = nseg - 1; // largest s with first[s] <= it and a non-empty range
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo + 1) / 2;
+        if (first[mid] <= it)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    item_inst[it] = uint32_t(lo);
+}
+
 } // namespace
 } // namespace optigpu
 
@@ -774,74 +820,60 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: out must be 8-byte aligned");
     if (offsets[0] < 0)
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: negative offset");
-    // One pass validates and counts: instances are the non-empty segments,
-    // items their 16384-element chunks.
-    int64_t ninst = 0, items = 0;
+    // One pass validates and counts the items (16384-element chunks).
+    int64_t items = 0;
     for (int32_t k = 0; k < nseg; ++k) {
         const int64_t len = offsets[k + 1] - offsets[k];
         if (len < 0 || offsets[k + 1] > (int64_t(1) << 40))
             return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: offsets must be non-decreasing and < 2^40");
-        if (len > 0) {
-            ++ninst;
-            items += (len + kReduceChunk - 1) / kReduceChunk;
-        }
+        items += (len + kReduceChunk - 1) / kReduceChunk;
     }
     const size_t es = esize_of(dtype);
     if (offsets[nseg] > offsets[0] && (!src || reinterpret_cast<uintptr_t>(src) % es))
         return fail(OPTIGPU_ERR_INVALID_ARG, "reduce_segmented: src must be non-null and element-aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Empty segments have no chunk: clear every result first.
-    optigpu_status st = check_cuda(cudaMemsetAsync(out, 0, 8 * size_t(nseg), s), "reduce_segmented: clear out");
-    if (st != OPTIGPU_OK || items == 0)
-        return st;
     const int config = 0;
-    const BatchLayout L = batch_layout(ninst, items, items);
+    // Workspace: the batch tables (instance s = segment s), then the offsets
+    // and every segment's first item, which the two table kernels expand.
+    const BatchLayout L = batch_layout(nseg, std::max<int64_t>(items, 1), std::max<int64_t>(items, 1));
+    const size_t meta_bytes = 2 * 8 * (size_t(nseg) + 1);
+    const size_t off_meta = (L.total + 255) / 256 * 256;
     void *ws = nullptr;
-    if ((st = stream_workspace(s, L.total, &ws, 1)) != OPTIGPU_OK)
+    optigpu_status st;
+    if ((st = stream_workspace(s, off_meta + meta_bytes, &ws, 1)) != OPTIGPU_OK)
         return st;
-    // The second pass writes [instances | item map] straight into pinned
-    // memory, copied in one asynchronous call.
-    const size_t image_bytes = L.off_part - L.off_inst;
     void *image = nullptr;
     cudaEvent_t copied = nullptr;
-    if ((st = seg_stage_buffer(s, image_bytes, &image, &copied)) != OPTIGPU_OK)
+    if ((st = seg_stage_buffer(s, meta_bytes, &image, &copied)) != OPTIGPU_OK)
         return st;
-    BatchInst *bi = static_cast<BatchInst *>(image);
-    uint32_t *map = reinterpret_cast<uint32_t *>(static_cast<char *>(image) + (L.off_items - L.off_inst));
-    uint32_t k_inst = 0;
+    int64_t *h_off = static_cast<int64_t *>(image);
+    int64_t *h_first = h_off + (nseg + 1);
+    std::memcpy(h_off, offsets, 8 * (size_t(nseg) + 1));
     int64_t it = 0;
     for (int32_t k = 0; k < nseg; ++k) {
-        const int64_t len = offsets[k + 1] - offsets[k];
-        if (len == 0)
-            continue;
-        BatchInst b;
-        std::memset(&b, 0, sizeof b);
-        b.src = static_cast<const char *>(src) + offsets[k] * int64_t(es);
-        b.dst = static_cast<char *>(out) + 8 * size_t(k);
-        b.rows = len;
-        b.cols = 1;
-        b.first_item = it;
-        b.aux = it; // one partial per chunk, in item order
-        b.op = OPTIGPU_OP_REDUCE;
-        b.dtype = int32_t(dtype);
-        const int64_t nit = (len + kReduceChunk - 1) / kReduceChunk;
-        b.nitems = int32_t(nit);
-        b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
-        bi[k_inst] = b;
-        for (int64_t j = 0; j < nit; ++j)
-            map[it + j] = k_inst;
-        it += nit;
-        ++k_inst;
+        h_first[k] = it;
+        it += (offsets[k + 1] - offsets[k] + kReduceChunk - 1) / kReduceChunk;
     }
+    h_first[nseg] = it;
     char *base = static_cast<char *>(ws);
-    if ((st = check_cuda(cudaMemcpyAsync(base + L.off_inst, image, image_bytes, cudaMemcpyHostToDevice, s),
-                         "reduce_segmented: upload tables")) != OPTIGPU_OK)
+    const int64_t *d_off = reinterpret_cast<const int64_t *>(base + off_meta);
+    const int64_t *d_first = d_off + (nseg + 1);
+    if ((st = check_cuda(cudaMemcpyAsync(base + off_meta, image, meta_bytes, cudaMemcpyHostToDevice, s),
+                         "reduce_segmented: upload offsets")) != OPTIGPU_OK)
         return st;
     if ((st = check_cuda(cudaEventRecord(copied, s), "reduce_segmented: staging event")) != OPTIGPU_OK)
         return st;
-    return batch_launch(config, reinterpret_cast<BatchInst *>(base + L.off_inst),
-                        reinterpret_cast<uint32_t *>(base + L.off_items), items,
-                        reinterpret_cast<unsigned long long *>(base + L.off_queue),
-                        reinterpret_cast<unsigned *>(base + L.off_done), ninst, base + L.off_part,
+    BatchInst *d_insts = reinterpret_cast<BatchInst *>(base + L.off_inst);
+    uint32_t *d_items = reinterpret_cast<uint32_t *>(base + L.off_items);
+    seg_instances_kernel<<<unsigned((nseg + 255) / 256), 256, 0, s>>>(
+        static_cast<const char *>(src), int64_t(es), int(dtype), static_cast<char *>(out), d_off, d_first, nseg,
+        d_insts);
+    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: instance table")) != OPTIGPU_OK || items == 0)
+        return st;
+    seg_items_kernel<<<unsigned((items + 255) / 256), 256, 0, s>>>(d_first, nseg, items, d_items);
+    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: item map")) != OPTIGPU_OK)
+        return st;
+    return batch_launch(config, d_insts, d_items, items, reinterpret_cast<unsigned long long *>(base + L.off_queue),
+                        reinterpret_cast<unsigned *>(base + L.off_done), nseg, base + L.off_part,
                         (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr);
 }
