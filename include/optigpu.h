@@ -73,7 +73,7 @@ typedef enum {
     OPTIGPU_OP_TRANSPOSE = 0,
     OPTIGPU_OP_REDUCE = 1,
     OPTIGPU_OP_BATCH = 2, /* autotuner only: the batch kernel's configurations */
-    OPTIGPU_OP_SCAN = 3   /* autotuner only: single-pass or three-pass inclusive scan */
+    OPTIGPU_OP_SCAN = 3   /* tuner: single-pass (0) or three-pass (1) inclusive scan */
 } optigpu_op;
 
 /* ------------------------------------------------------------------------ */
@@ -450,8 +450,8 @@ int optigpu_tune_selected(optigpu_op op, optigpu_dtype dtype);
 optigpu_status optigpu_tune_set_param(const char *name, int64_t value);
 int64_t optigpu_tune_get_param(const char *name); /* -1 if unknown */
 
-/* Times every configuration of `op` on a rows x cols problem (the sum uses
- * n = rows * cols) in library-owned scratch memory (cudaMalloc'd and freed
+/* Times every configuration of `op` on a rows x cols problem (the sum and
+ * the scan use n = rows * cols) in library-owned scratch memory (cudaMalloc'd and freed
  * inside the call), `reps` timed launches each after two warm-ups, median of
  * CUDA-event times on `stream`; selects the fastest and returns its index
  * and time.  Transpose TMA configurations are skipped when the shape is not

@@ -173,7 +173,7 @@ int64_t optigpu_tune_get_param(const char *name)
 optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows, int64_t cols, int reps,
                                 optigpu_stream_t stream, int *best_config, float *best_ms)
 {
-    if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH || op == OPTIGPU_OP_SCAN)
+    if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH || !dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: unknown op or dtype (batches: optigpu_batch_autotune)");
     if (rows <= 0 || cols <= 0 || rows > (int64_t(1) << 31) || cols > (int64_t(1) << 31) || reps < 1 ||
         reps > 1000)
@@ -195,6 +195,11 @@ optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows
     if (op == OPTIGPU_OP_REDUCE &&
         (st = check_cuda(cudaMalloc(&b.p, 8), "autotune: cudaMalloc")) != OPTIGPU_OK)
         return st;
+    const int64_t n_elems = rows * cols;
+    if (op == OPTIGPU_OP_SCAN &&
+        (st = check_cuda(cudaMalloc(&b.p, size_t(n_elems) * (dtype == OPTIGPU_INT32 ? 8 : 4)),
+                         "autotune: cudaMalloc")) != OPTIGPU_OK)
+        return st;
     out = static_cast<double *>(b.p);
     const int n = optigpu_tune_num_configs(op, dtype);
     const int prev = optigpu_tune_selected(op, dtype);
@@ -206,6 +211,9 @@ optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows
             if (c + 1 < n && !optigpu_transpose_tma_eligible(a.p, b.p, rows, cols, dtype))
                 continue;
             st = time_median([&] { return transpose_launch_config(a.p, b.p, rows, cols, es, c, s); }, reps, s, ms);
+        } else if (op == OPTIGPU_OP_SCAN) {
+            scan_select(c);
+            st = time_median([&] { return optigpu_scan_inclusive(a.p, b.p, n_elems, dtype, s); }, reps, s, ms);
         } else {
             reduce_select(c);
             st = time_median([&] { return reduce_dispatch(a.p, rows * cols, int(dtype), out, 0u, s); }, reps, s, ms);
@@ -213,6 +221,8 @@ optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows
         if (st != OPTIGPU_OK) {
             if (op == OPTIGPU_OP_REDUCE)
                 reduce_select(prev);
+            if (op == OPTIGPU_OP_SCAN)
+                scan_select(prev);
             return st;
         }
         if (best < 0 || ms < best_t) {

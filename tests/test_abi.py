@@ -152,7 +152,7 @@ def test_batch_plan_rejects_bad_flags_and_tables(lib):
 
 def test_tune_tables_are_host_only(lib):
     for op, dt in ((N.OP_TRANSPOSE, N.FLOAT32), (N.OP_TRANSPOSE, N.BFLOAT16), (N.OP_REDUCE, N.FLOAT32),
-                   (N.OP_BATCH, 0)):
+                   (N.OP_BATCH, 0), (N.OP_SCAN, 0)):
         n = lib.optigpu_tune_num_configs(op, dt)
         assert n >= 2
         names = [lib.optigpu_tune_config_name(op, dt, i) for i in range(n)]
@@ -177,6 +177,19 @@ def test_tune_cache_round_trip(lib, tmp_path):
     assert lib.optigpu_tune_load(b"/nonexistent/tune.txt") == N.ERR_NOT_FOUND
     lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 0)
     lib.optigpu_tune_set_param(b"transpose.group_rows", 16)
+
+
+def test_tune_cache_keeps_the_scan_form(lib, tmp_path):
+    path = str(tmp_path / "tune_scan.txt").encode()
+    assert lib.optigpu_tune_selected(N.OP_SCAN, 0) == 0          # single pass by default
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 1) == N.OK
+    assert lib.optigpu_tune_save(path) == N.OK
+    assert b"scan " in open(path, "rb").read()
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
+    assert lib.optigpu_tune_load(path) == N.OK
+    assert lib.optigpu_tune_selected(N.OP_SCAN, 0) == 1
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 2) == N.ERR_INVALID_ARG
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
 
 
 def test_server_validation_is_host_side(lib):

@@ -212,6 +212,17 @@ def test_scan_infinities_and_nan(n, scan_config):
     assert (np.abs(got[fin] - want[fin]) <= 1e-6 * scale[fin] + 1e-30).all()
 
 
+def test_scan_autotune_selects_a_form():
+    best, name, ms = api.autotune("scan", torch.float32, 1 << 12, 1 << 12, reps=3)
+    assert best in (0, 1) and ms > 0 and name == api.tune_configs("scan", torch.float32)[best]
+    assert api.tune_selected("scan", torch.float32) == best
+    a = workloads.vector(100003, "float32", seed=12)
+    got = api.scan(to_device(a, "float32")).cpu().numpy().astype(np.float64)
+    scale = oracle.scan(np.abs(a), "float32")
+    assert (np.abs(got - oracle.scan(a, "float32")) <= 1e-6 * scale + 1e-30).all()
+    api.tune_select("scan", torch.float32, 0)
+
+
 def test_scan_repeatable_many_chunks(scan_config):
     # 2^24 fp32 = 4096 single-pass chunks: bit-identical over repeated runs.
     f = workloads.vector(1 << 24, "float32", seed=9)
