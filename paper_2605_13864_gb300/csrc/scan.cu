@@ -267,15 +267,16 @@ struct ScanLevels {
 // A published block sum is two 64-bit words, each a nonzero tag over one
 // 32-bit half of the value, so a reader that sees both tags has the whole
 // value: no fence orders the halves (the slots start zeroed every launch).
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+// Both words move in one 16-byte GPU-scope access; each 8-byte element is
+// still a single-copy-atomic relaxed access, which is all the tags need.
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a, unsigned long long b)
 {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
+                                              unsigned long long &b)
 {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 template <typename C>
@@ -284,14 +285,14 @@ __device__ __forceinline__ void publish_block(unsigned long long *slot, C v)
     static_assert(sizeof(C) == 8, "64-bit carries");
     unsigned long long bits;
     memcpy(&bits, &v, 8);
-    st_relaxed_u64(slot, (1ull << 32) | (bits & 0xffffffffull));
-    st_relaxed_u64(slot + 1, (1ull << 32) | (bits >> 32));
+    st_relaxed_v2(slot, (1ull << 32) | (bits & 0xffffffffull), (1ull << 32) | (bits >> 32));
 }
 
 template <typename C>
 __device__ __forceinline__ bool try_block(const unsigned long long *slot, C &v)
 {
-    const unsigned long long a = ld_relaxed_u64(slot), b = ld_relaxed_u64(slot + 1);
+    unsigned long long a, b;
+    ld_relaxed_v2(slot, a, b);
     if ((a >> 32) == 0ull || (b >> 32) == 0ull)
         return false;
     const unsigned long long bits = (a & 0xffffffffull) | (b << 32);
