@@ -351,7 +351,7 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
         sv = api.Server(budget_bytes=40 << 30, max_slots=256, n_streams=streams, per_call=per_call)
         sv.replay(host[:1000], np.zeros(1000))
         points = []
-        for rate_k in (20, 50, 100, 150, 200, 300, 400):
+        for rate_k in (20, 50, 100, 150, 200, 225, 250, 275, 300, 400):
             arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / (rate_k * 1e3), sweep_n))
             t0 = time.perf_counter()
             lat = sv.replay(host[:sweep_n], arr)
