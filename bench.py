@@ -51,8 +51,8 @@ METRIC = "transpose/reduce HBM GB/s (% of GB300 peak)"
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
 # TRANSPOSE_SOURCES below).
-NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073980672 + 1027606784,
-                         "src_sha256": "a7a44b0acf56362b8279f6916a547453ae0f9524ce086c5a8f45528cacc0cccf"}
+NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073773312 + 1027839232,
+                         "src_sha256": "48247ea6bce93014c160bbc09323379cc51639007543f4bbc490bd5655484b65"}
 
 
 def _peaks():
@@ -632,6 +632,8 @@ def run_gpu(args):
                 "transpose_frac_of_8tbs": round(achieved / 8000.0, 4),
                 "reduce_ms": round(r_avg, 4), "reduce_gbs": round(R_BYTES / (r_avg * 1e-3) / 1e9, 1),
                 "reduce_frac_of_peak": round(R_BYTES / (r_avg * 1e-3) / 1e9 / peak, 4),
+                "transpose_ms_p10_p50_p90": [round(float(np.percentile(t_ms, q)), 4) for q in (10, 50, 90)],
+                "reduce_ms_p10_p50_p90": [round(float(np.percentile(r_ms, q)), 4) for q in (10, 50, 90)],
             },
             "e2e": {"value": round(job_value(world, STEP_BYTES, e2e_s * 1e3), 3), "unit": "GB/s",
                     "h2d_bytes_per_step": ROWS * COLS * ESIZE + N_SUM * ESIZE,

@@ -561,6 +561,7 @@ extern "C" {
 optigpu_status optigpu_batch_plan_create(const optigpu_desc *descs, int32_t count, uint32_t flags,
                                          optigpu_batch_plan **plan)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_batch_plan_create");
     if (!plan)
         return fail(OPTIGPU_ERR_INVALID_ARG, "batch: null plan pointer");
     *plan = nullptr;
@@ -596,6 +597,7 @@ optigpu_status optigpu_batch_plan_create(const optigpu_desc *descs, int32_t coun
 
 optigpu_status optigpu_batch_run(optigpu_batch_plan *plan, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_batch_run");
     if (!plan)
         return fail(OPTIGPU_ERR_INVALID_ARG, "batch: null plan");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -638,6 +640,7 @@ optigpu_status optigpu_batch_plan_info(const optigpu_batch_plan *plan, int64_t *
 optigpu_status optigpu_batch_autotune(optigpu_batch_plan *plan, int reps, optigpu_stream_t stream,
                                       int *best_config, float *best_ms)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_batch_autotune");
     if (!plan || reps < 1 || reps > 1000)
         return fail(OPTIGPU_ERR_INVALID_ARG, "batch_autotune: null plan or reps outside [1, 1000]");
     if (plan->total_items == 0)
@@ -807,6 +810,7 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
                                                    optigpu_dtype dtype, void *out, uint32_t flags,
                                                    optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_reduce_segmented");
     using namespace optigpu;
     if (!dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce_segmented: unknown dtype");

@@ -104,6 +104,7 @@ using namespace optigpu;
 extern "C" optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, int64_t lo, int64_t width,
                                                 int32_t nbins, int64_t *counts, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_histogram_i32");
     if (n < 0 || width < 1 || nbins < 1 || nbins > (1 << 26))
         return fail(OPTIGPU_ERR_INVALID_ARG, "histogram: need n >= 0, width >= 1, 1 <= nbins <= 2^26");
     if (!counts || reinterpret_cast<uintptr_t>(counts) % 8 || (n > 0 && (!src || reinterpret_cast<uintptr_t>(src) % 4)))

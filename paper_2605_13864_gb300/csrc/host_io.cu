@@ -144,6 +144,7 @@ extern "C" {
 optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int64_t rows, int64_t cols,
                                       optigpu_dtype dtype, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_transpose_host");
     if (!dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_host: unknown dtype");
     if (rows < 0 || cols < 0)
@@ -218,6 +219,7 @@ optigpu_status optigpu_transpose_host(const void *host_src, void *host_dst, int6
 optigpu_status optigpu_reduce_sum_host(const void *host_src, int64_t n, optigpu_dtype dtype, void *host_out,
                                        uint32_t flags, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_reduce_sum_host");
     if (!dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "reduce_sum_host: unknown dtype");
     if (flags & ~OPTIGPU_REDUCE_COMPENSATED)

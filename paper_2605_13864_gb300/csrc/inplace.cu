@@ -274,6 +274,7 @@ extern "C" {
 
 optigpu_status optigpu_transpose_inplace(void *a, int64_t n, optigpu_dtype dtype, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_transpose_inplace");
     if (!dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "transpose_inplace: unknown dtype");
     if (n < 0 || n > (int64_t(1) << 30))

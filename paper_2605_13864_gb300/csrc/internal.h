@@ -9,10 +9,21 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/optigpu.h"
 
 namespace optigpu {
+
+// NVTX range around a public entry point: a named span in Nsight timelines,
+// a pointer test when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 // Codes written to the device status word by kernels (bit flags).
 enum : unsigned {

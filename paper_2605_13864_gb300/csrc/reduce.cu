@@ -273,6 +273,7 @@ optigpu_status optigpu_reduce_sum(const void *src, int64_t n, optigpu_dtype dtyp
 optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n, optigpu_dtype dtype, void *out,
                                      uint32_t flags, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_reduce_sum_ex");
     return reduce_dispatch(src, n, int(dtype), out, flags, static_cast<cudaStream_t>(stream));
 }
 

@@ -773,6 +773,7 @@ using namespace optigpu;
 extern "C" optigpu_status optigpu_scan_inclusive(const void *src, void *dst, int64_t n, optigpu_dtype dtype,
                                                  optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_scan_inclusive");
     if (!dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_UNSUPPORTED_DTYPE, "scan: unknown dtype");
     if (n < 0 || n > (int64_t(1) << 40))

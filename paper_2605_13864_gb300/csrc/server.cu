@@ -577,6 +577,7 @@ optigpu_status optigpu_server_submit(optigpu_server *sv, const optigpu_request *
 
 optigpu_status optigpu_server_step(optigpu_server *sv, int32_t *launched)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_server_step");
     if (!sv)
         return fail(OPTIGPU_ERR_INVALID_ARG, "server: null server");
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -633,6 +634,7 @@ optigpu_status optigpu_server_get_stats(optigpu_server *sv, optigpu_server_stats
 optigpu_status optigpu_server_replay(optigpu_server *sv, const optigpu_request *reqs, const double *arrival_s,
                                      int64_t count, double *latency_s)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_server_replay");
     if (!sv || count < 0 || (count > 0 && (!reqs || !arrival_s || !latency_s)))
         return fail(OPTIGPU_ERR_INVALID_ARG, "server_replay: bad arguments");
     for (int64_t i = 1; i < count; ++i)

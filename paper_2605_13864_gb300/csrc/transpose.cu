@@ -570,12 +570,14 @@ optigpu_status optigpu_transpose_ex(const void *src, void *dst, int64_t rows, in
                                     optigpu_dtype dtype, optigpu_transpose_kernel kernel,
                                     optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_transpose_ex");
     return transpose_dispatch(src, dst, rows, cols, int(dtype), int(kernel), static_cast<cudaStream_t>(stream));
 }
 
 optigpu_status optigpu_transpose_strided(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t rows,
                                          int64_t cols, optigpu_dtype dtype, optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_transpose_strided");
     return transpose_dispatch_pitched(src, lds, dst, ldd, rows, cols, int(dtype), OPTIGPU_TRANSPOSE_AUTO,
                                       static_cast<cudaStream_t>(stream));
 }
@@ -584,6 +586,7 @@ optigpu_status optigpu_transpose_batched(const void *src, int64_t stride_src, vo
                                          int64_t batch, int64_t rows, int64_t cols, optigpu_dtype dtype,
                                          optigpu_stream_t stream)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_transpose_batched");
     return transpose_batched_dispatch(src, stride_src, dst, stride_dst, batch, rows, cols, int(dtype),
                                       static_cast<cudaStream_t>(stream));
 }

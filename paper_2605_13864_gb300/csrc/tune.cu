@@ -173,6 +173,7 @@ int64_t optigpu_tune_get_param(const char *name)
 optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows, int64_t cols, int reps,
                                 optigpu_stream_t stream, int *best_config, float *best_ms)
 {
+    optigpu::NvtxRange nvtx_range("optigpu_autotune");
     if (!op_dtype_ok(op, dtype) || op == OPTIGPU_OP_BATCH || !dtype_valid(int(dtype)))
         return fail(OPTIGPU_ERR_INVALID_ARG, "autotune: unknown op or dtype (batches: optigpu_batch_autotune)");
     if (rows <= 0 || cols <= 0 || rows > (int64_t(1) << 31) || cols > (int64_t(1) << 31) || reps < 1 ||
