@@ -431,7 +431,8 @@ def measure_next(reps: int = 10):
     """The neighbouring problems at roofline scale, CUDA-event timed:
     batched transpose (64 x 2048^2 fp32), in-place transpose (16384^2 fp32),
     segmented sums (2^28 fp32 in 16384 segments), inclusive scans (2^28 int32
-    -> int64, 2^28 fp32 -> fp32) and the int32 histogram (2^28 values,
+    -> int64, fp32 -> fp32 and bf16 -> fp32, each tuner form) and the int32
+    histogram (2^28 values,
     4096 bins).  Bytes follow the same convention: every input byte read
     once plus every output byte written once."""
     import torch
@@ -477,13 +478,15 @@ def measure_next(reps: int = 10):
     vi = torch.randint(0, 4096, (1 << 28,), dtype=torch.int32, device="cuda", generator=g)
     out32 = torch.empty(1 << 28, device="cuda")
     out64 = torch.empty(1 << 28, dtype=torch.int64, device="cuda")
+    vb = v.to(torch.bfloat16)
     scan_default = api.tune_selected("scan", torch.float32)
-    for cfg, tag in ((0, ""), (1, "_three_pass")):
+    for cfg, tag in ((0, ""), (1, "_three_pass"), (2, "_carries_at_once")):
         api.tune_select("scan", torch.float32, cfg)
         timed("scan_2p28_fp32" + tag, lambda: api.scan(v, out=out32), (1 << 28) * 8)
         timed("scan_2p28_int32_to_int64" + tag, lambda: api.scan(vi, out=out64), (1 << 28) * 12)
+        timed("scan_2p28_bf16_to_fp32" + tag, lambda: api.scan(vb, out=out32), (1 << 28) * 6)
     api.tune_select("scan", torch.float32, scan_default)
-    del out32, out64
+    del out32, out64, vb
     timed("histogram_2p28_int32_4096bins", lambda: api.histogram(vi, 0, 1, 4096), (1 << 28) * 4)
     del v, vi
     torch.cuda.empty_cache()
@@ -694,7 +697,7 @@ def run_case(args):
             plan.run()
         torch.cuda.synchronize()
         plan.close()
-    elif case in ("scan_f32", "scan_i32", "scan3_f32", "scan3_i32"):
+    elif case in ("scan_f32", "scan_i32", "scan3_f32", "scan3_i32", "scan2_f32", "scan2_i32"):
         n = side * side
         if case.endswith("f32"):
             v = torch.randn(n, device="cuda")
@@ -702,7 +705,7 @@ def run_case(args):
         else:
             v = torch.randint(0, 4096, (n,), dtype=torch.int32, device="cuda")
             o = torch.empty(n, dtype=torch.int64, device="cuda")
-        api.tune_select("scan", torch.float32, 1 if case.startswith("scan3") else 0)
+        api.tune_select("scan", torch.float32, 1 if case.startswith("scan3") else 2 if case.startswith("scan2") else 0)
         for _ in range(args.case_reps):
             api.scan(v, out=o)
     elif case == "histogram":
@@ -749,7 +752,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, "
-                         "scan_f32, scan_i32, scan3_f32, scan3_i32, histogram, inplace_f32, "
+                         "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, histogram, inplace_f32, "
                          "transpose_batched_f32, segmented_f32)")
     ap.add_argument("--side", type=int, default=8192)
     ap.add_argument("--count", type=int, default=1024)

@@ -73,7 +73,7 @@ typedef enum {
     OPTIGPU_OP_TRANSPOSE = 0,
     OPTIGPU_OP_REDUCE = 1,
     OPTIGPU_OP_BATCH = 2, /* autotuner only: the batch kernel's configurations */
-    OPTIGPU_OP_SCAN = 3   /* tuner: single-pass (0) or three-pass (1) inclusive scan */
+    OPTIGPU_OP_SCAN = 3   /* tuner: form of the inclusive scan (0, 1, 2; see optigpu_scan_inclusive) */
 } optigpu_op;
 
 /* ------------------------------------------------------------------------ */
@@ -197,16 +197,19 @@ optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets,
  *                     FP32 inside each 4096-element sub-block, FP64 carries
  *                     between sub-blocks and chunks; within 1e-6 of the sum
  *                     of |x| over the prefix.
- * Default: one pass over 4096-element chunks claimed in order; the carry of
- * chunk c is a sum of aligned power-of-two blocks of earlier chunk totals
- * (pairwise sums, the blocks of the binary decomposition of c added largest
- * first), an expression fixed by c, so the result is bit-identical from run
- * to run (device waits bounded; a wait that gives up is reported by
- * optigpu_stream_status).  The three-launch form (chunk sums, carries, chunk
- * scans) is the tuner's configuration 1 (OPTIGPU_OP_SCAN).  src and dst must
- * not overlap; n in [0, 2^40].  Uses a per-stream library workspace of about
- * 10 bytes per 1024 elements.  Errors as
- * optigpu_reduce_sum_ex, plus OVERLAP. */
+ * Default: one pass over 4096-element chunks claimed in order.  Block (k, m)
+ * is the sum of the totals of chunks [m 32^k, (m+1) 32^k), formed by a fixed
+ * butterfly over its 32 children; the carry of chunk c adds, level by level
+ * from the top, the complete blocks before c inside its parent group (the
+ * base-32 digits of c).  The expression is fixed by c, so the result is
+ * bit-identical from run to run (device waits bounded; a wait that gives up
+ * is reported by optigpu_stream_status).  Tuner configurations
+ * (OPTIGPU_OP_SCAN): 0 = the single pass with each carry used one chunk
+ * after it is fetched (default), 1 = three launches (chunk sums, carries,
+ * chunk scans), 2 = the single pass reading each carry at once; 0 and 2
+ * give the same bits.  src and dst must not overlap; n in [0, 2^40].  Uses a
+ * per-stream library workspace of about 4 bytes per 1024 elements.  Errors
+ * as optigpu_reduce_sum_ex, plus OVERLAP. */
 optigpu_status optigpu_scan_inclusive(const void *src, void *dst, int64_t n,
                                       optigpu_dtype dtype, optigpu_stream_t stream);
 
@@ -430,7 +433,8 @@ void optigpu_server_destroy(optigpu_server *server);
 /* Number of configurations of `op` for `dtype` (-1 for a bad op or dtype).
  * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel.
  * OPTIGPU_OP_BATCH ignores `dtype`; its selection is the default of new
- * plans.  OPTIGPU_OP_SCAN ignores `dtype`: 0 = single pass, 1 = three passes. */
+ * plans.  OPTIGPU_OP_SCAN ignores `dtype`: 0 = single pass (carries used
+ * one chunk later), 1 = three passes, 2 = single pass (carries read at once). */
 int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype);
 
 /* Static name of configuration `config`, or NULL if out of range. */

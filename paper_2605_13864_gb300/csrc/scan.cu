@@ -2,10 +2,13 @@
 // (the thesis names parallel prefix sum as future work, Sec. 9; the running
 // sum of Listing 2.1's loop, keeping every intermediate value).
 //
-// Default: one pass (scan_onepass_kernel below): 4096-element chunks claimed
-// in order, TMA-staged, each carried by a sum of dyadic blocks of earlier
+// Default: one pass (scan_deferred_kernel below): 4096-element chunks claimed
+// in order, TMA-staged, each carried by a sum of radix-32 blocks of earlier
 // chunk totals whose expression depends on the chunk index alone, so results
 // are bit-identical from run to run and no chunk waits on another's carry.
+// Each carry is fetched one chunk after the scan that publishes its own
+// chunk and used one chunk later still; scan_onepass_kernel, configuration
+// 2, is the same pass reading each carry at once.
 // The three-launch form, kept as configuration 1, runs in a fixed order too:
 //   1. chunk sums: the sum's own kernel (reduce_band) writes one FP64 / int64
 //      partial per 16384-element chunk;
@@ -288,16 +291,23 @@ __device__ __forceinline__ void publish_block(unsigned long long *slot, C v)
     st_relaxed_v2(slot, (1ull << 32) | (bits & 0xffffffffull), (1ull << 32) | (bits >> 32));
 }
 
+// Decodes the two words of a slot; false while either tag is still zero.
 template <typename C>
-__device__ __forceinline__ bool try_block(const unsigned long long *slot, C &v)
+__device__ __forceinline__ bool decode_block(unsigned long long a, unsigned long long b, C &v)
 {
-    unsigned long long a, b;
-    ld_relaxed_v2(slot, a, b);
     if ((a >> 32) == 0ull || (b >> 32) == 0ull)
         return false;
     const unsigned long long bits = (a & 0xffffffffull) | (b << 32);
     memcpy(&v, &bits, 8);
     return true;
+}
+
+template <typename C>
+__device__ __forceinline__ bool try_block(const unsigned long long *slot, C &v)
+{
+    unsigned long long a, b;
+    ld_relaxed_v2(slot, a, b);
+    return decode_block<C>(a, b, v);
 }
 
 // Bounded wait for a block sum; gives up after limit_ns (value 0).
@@ -339,6 +349,10 @@ struct OnePass {
     static constexpr int kInRow = 128 / kInBytes;  // elements per 128-byte row
     static constexpr int kOutRow = 128 / kOutBytes;
     static constexpr int kMinBlocks = 3; // CTAs per SM the register budget is sized for
+    // Deferred-carry form: a three-stage input ring; int32 (8-byte outputs)
+    // fits two CTAs per SM, the float types three.
+    static constexpr int kSmemDeferred = 3 * kInStage + kOutStage + 1024;
+    static constexpr int kMinBlocksDeferred = kOutBytes == 8 ? 2 : 3;
 };
 
 // Element bits (the low 16 bits for 2-byte types) -> in-chunk accumulator.
@@ -649,10 +663,351 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
         atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
 }
 
-std::atomic<int> g_scan_choice{0}; // 0: single pass, 1: three passes
+// The same single pass with every carry used one iteration later.  Warp w
+// (w < levels) fetches level w of the carry of chunk k-1 right after the scan
+// of chunk k -- when the form above reads it -- with one bulk copy into
+// shared memory, and reduces it after the scan of chunk k+1.  The round trip
+// overlaps a whole iteration, and no CTA barrier waits for it: a bulk copy
+// completes on an mbarrier of its own.  Chunk k-1 stays in the third stage
+// of a three-stage input ring and is reloaded into registers at the end of
+// iteration k, so it is finished from its raw words by the same operations
+// as in the form above, giving the same bits.  Warp 7 publishes totals and
+// forms blocks.
+//   iteration k:  wait for chunk k in in[k % 3]; thread 0 loads chunk k+1
+//                 into in[(k+1) % 3] (its previous chunk, k-2, went to
+//                 registers one iteration ago) and claims chunk k+2; scan
+//                 chunk k; warp 7 publishes it; warps 0..levels-1 reduce the
+//                 carry levels of chunk k-2 and start the copies for chunk
+//                 k-1; chunk k-2 gets its carry and leaves through the
+//                 swizzled out stage and one TMA store; chunk k-1 is reloaded
+//                 from in[(k-1) % 3].
+template <int DT>
+__global__ void __launch_bounds__(kScanThreads, OnePass<DT>::kMinBlocksDeferred)
+scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
+                     const void *__restrict__ src, void *__restrict__ dst, int64_t n, int64_t num_chunks,
+                     int64_t full_chunks, int in_tma, int out_tma, unsigned long long *ticket, unsigned *groups,
+                     unsigned long long *blocks, const __grid_constant__ ScanLevels L, uint64_t wait_limit_ns,
+                     unsigned *err)
+{
+    using P = OnePass<DT>;
+    using T = ScanTraits<DT>;
+    using Acc = typename T::Acc;
+    using Carry = typename T::Carry;
+    using Out = typename T::Out;
+    constexpr int kWords = P::kPer * P::kInBytes / 4; // raw 32-bit words per thread
+    constexpr int kPubWarp = kScanThreads / 32 - 1;
+    static_assert(kMaxLevels <= kPubWarp, "one warp per carry level, one to publish");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[3];
+    __shared__ __align__(8) uint64_t slot_bar[kMaxLevels];
+    __shared__ __align__(16) unsigned long long s_slot[kMaxLevels][64]; // 32 slots of two words per level
+    __shared__ Acc warp_tot[kScanThreads / 32];
+    __shared__ int64_t s_chunk[3];
+    __shared__ Carry s_level[kMaxLevels];
+
+    const uint32_t raw_addr = ptx::smem_addr(smem_raw);
+    const uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
+    unsigned char *stage = smem_raw + pad;
+    const uint32_t stage_addr = raw_addr + pad; // in[0] | in[1] | in[2] | out
+    const uint32_t out_addr = stage_addr + 3 * P::kInStage;
+    const unsigned char *out_stage = stage + 3 * P::kInStage;
+    const uint32_t bar0 = ptx::smem_addr(&full_bar[0]);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t my_slot_bar = ptx::smem_addr(&slot_bar[warp < kMaxLevels ? warp : 0]);
+    bool failed = false;
+
+    if (t == 0) {
+        for (int s = 0; s < 3; ++s)
+            ptx::mbar_init(bar0 + 8u * s, 1);
+        for (int k = 0; k < kMaxLevels; ++k)
+            ptx::mbar_init(ptx::smem_addr(&slot_bar[k]), 1);
+        ptx::fence_mbar_init();
+        if (in_tma)
+            ptx::prefetch_tensormap(&in_map);
+        if (out_tma)
+            ptx::prefetch_tensormap(&out_map);
+        const int64_t c0 = int64_t(atomicAdd(ticket, 1ull));
+        s_chunk[0] = c0;
+        if (in_tma && c0 < full_chunks) {
+            ptx::mbar_arrive_expect_tx(bar0, P::kInStage);
+            ptx::tma_load_3d(stage_addr, &in_map, 0, 0, int32_t(c0), bar0);
+        }
+        s_chunk[1] = c0 < num_chunks ? int64_t(atomicAdd(ticket, 1ull)) : num_chunks;
+    }
+    __syncthreads();
+
+    uint32_t raw_prev2[kWords]; // raw words of chunk prev2 (reloaded one iteration ago)
+    Acc before_p1 = Acc(0), before_p2 = Acc(0);
+    int64_t prev1 = -1, prev2 = -1; // chunks scanned one and two iterations ago (uniform)
+    bool drained = false;
+    bool slot_pending = false; // this warp's slot copy is in flight
+    uint32_t phase = 0;        // bit s: parity of the next completion of in[s]
+    uint32_t slot_phase = 0;   // parity of the next completion of this warp's slot copy
+    for (int it = 0;; ++it) {
+        const int sidx = it % 3;
+        const int64_t c = drained ? num_chunks : s_chunk[sidx];
+        const bool has_cur = c < num_chunks;
+        drained = !has_cur;
+        if (!has_cur && prev1 < 0 && prev2 < 0)
+            break;
+        const int64_t base = c * P::kChunk;
+        const uint32_t in_addr = stage_addr + uint32_t(sidx) * P::kInStage;
+        unsigned long long claim = 0;
+        Acc before = Acc(0);
+        if (has_cur) {
+            if (in_tma && c < full_chunks) {
+                const uint32_t fb = bar0 + 8u * uint32_t(sidx);
+                const bool ok = ptx::mbar_wait_bounded(fb, (phase >> sidx) & 1u, wait_limit_ns);
+                phase ^= 1u << sidx;
+                if (__syncthreads_or(!ok)) {
+                    // The copy did not arrive in time: give it one more
+                    // bounded wait, report, and stop.
+                    if (t == 0) {
+                        ptx::mbar_wait_bounded(fb, ((phase >> sidx) & 1u) ^ 1u, wait_limit_ns);
+                        atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
+                    }
+                    break;
+                }
+            } else {
+                unsigned char *in_ptr = stage + sidx * P::kInStage;
+#pragma unroll
+                for (int k = 0; k < P::kPer; ++k) {
+                    const int e = t + k * kScanThreads;
+                    const int64_t i = base + e;
+                    const uint32_t off = swz128(uint32_t(e * P::kInBytes));
+                    if constexpr (P::kInBytes == 4)
+                        *reinterpret_cast<uint32_t *>(in_ptr + off) =
+                            i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
+                    else
+                        *reinterpret_cast<uint16_t *>(in_ptr + off) =
+                            i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
+                }
+                __syncthreads();
+            }
+            if (t == 0) {
+                // Load the chunk claimed last iteration into the next stage
+                // of the ring and claim the one after it; the claim is
+                // stored only after the scan, so its round trip overlaps it.
+                const int nidx = (it + 1) % 3;
+                const int64_t cn = s_chunk[nidx];
+                if (in_tma && cn < full_chunks) {
+                    const uint32_t nb = bar0 + 8u * uint32_t(nidx);
+                    ptx::mbar_arrive_expect_tx(nb, P::kInStage);
+                    ptx::tma_load_3d(stage_addr + uint32_t(nidx) * P::kInStage, &in_map, 0, 0, int32_t(cn), nb);
+                }
+                claim = cn < num_chunks ? atomicAdd(ticket, 1ull) : (unsigned long long)num_chunks;
+            }
+            // Thread t scans elements 16 t .. 16 t + 15 of the chunk.
+            const uint32_t region = uint32_t(t) * P::kPer * P::kInBytes;
+            uint32_t raw[kWords];
+#pragma unroll
+            for (int q = 0; q < kWords / 4; ++q) {
+                const uint4 w = ptx::lds_v4(in_addr + swz128(region + 16u * q));
+                raw[4 * q] = w.x;
+                raw[4 * q + 1] = w.y;
+                raw[4 * q + 2] = w.z;
+                raw[4 * q + 3] = w.w;
+            }
+            Acc run = Acc(0);
+#pragma unroll
+            for (int w = 0; w < kWords; ++w) {
+                if constexpr (P::kInBytes == 4) {
+                    run += acc_of_bits<DT>(raw[w]);
+                } else {
+                    run += acc_of_bits<DT>(raw[w] & 0xffffu);
+                    run += acc_of_bits<DT>(raw[w] >> 16);
+                }
+            }
+            Acc total;
+            before = block_exclusive_scan<Acc>(run, warp_tot, &total);
+            if (warp == kPubWarp) {
+                // Publish B(0, c), then form every block this chunk completes
+                // as the 32nd arrival of its group.
+                if (lane == 0)
+                    publish_block<Carry>(blocks + 2 * (L.block_off[0] + uint64_t(c)), Carry(total));
+                int64_t j = c;
+                for (int k = 0; k + 1 < L.levels; ++k) {
+                    const int64_t parent = j >> kRadixLog;
+                    if (((parent + 1) << kRadixLog) > L.count[k])
+                        break; // an incomplete group is never needed
+                    unsigned last = 0;
+                    if (lane == 0)
+                        last = atomicAdd(groups + L.group_off[k] + uint64_t(parent), 1u) == 31u;
+                    if (!__shfl_sync(0xffffffffu, last, 0))
+                        break; // later arrivals form it
+                    Carry x;
+                    if (!wait_block<Carry>(blocks + 2 * (L.block_off[k] + uint64_t((parent << kRadixLog) + lane)), x,
+                                           wait_limit_ns))
+                        failed = true;
+#pragma unroll
+                    for (int d = 16; d; d >>= 1)
+                        x += __shfl_xor_sync(0xffffffffu, x, d);
+                    if (lane == 0)
+                        publish_block<Carry>(blocks + 2 * (L.block_off[k + 1] + uint64_t(parent)), x);
+                    j = parent;
+                }
+            }
+        }
+
+        if (warp < L.levels) {
+            // Level `warp` of the carry of chunk prev2 (its slots were copied
+            // one iteration ago), then the copy for chunk prev1.
+            const int lvl = warp;
+            if (prev2 > 0) {
+                const int d = int((prev2 >> (kRadixLog * lvl)) & 31);
+                Carry x = Carry(0);
+                if (d > 0) { // uniform across the warp
+                    if (!ptx::mbar_wait_bounded(my_slot_bar, slot_phase, wait_limit_ns))
+                        failed = true;
+                    slot_phase ^= 1u;
+                    slot_pending = false;
+                    if (lane < d && !decode_block<Carry>(s_slot[lvl][2 * lane], s_slot[lvl][2 * lane + 1], x) &&
+                        !wait_block<Carry>(blocks + 2 * (L.block_off[lvl] +
+                                                         uint64_t(((prev2 >> (kRadixLog * (lvl + 1))) << kRadixLog) +
+                                                                  lane)),
+                                           x, wait_limit_ns))
+                        failed = true; // copied before it was published: read it again
+                    if (lane >= d)
+                        x = Carry(0);
+#pragma unroll
+                    for (int dd = 16; dd; dd >>= 1)
+                        x += __shfl_xor_sync(0xffffffffu, x, dd);
+                }
+                if (lane == 0)
+                    s_level[lvl] = x;
+            }
+            if (prev1 > 0) {
+                const int d = int((prev1 >> (kRadixLog * lvl)) & 31);
+                if (d > 0) { // uniform across the warp
+                    __syncwarp(); // every lane has read its slot of the last copy
+                    if (lane == 0) {
+                        ptx::fence_proxy_async_smem();
+                        ptx::mbar_arrive_expect_tx(my_slot_bar, 16u * uint32_t(d));
+                        ptx::bulk_load(ptx::smem_addr(&s_slot[lvl][0]),
+                                       blocks + 2 * (L.block_off[lvl] +
+                                                     uint64_t((prev1 >> (kRadixLog * (lvl + 1))) << kRadixLog)),
+                                       16u * uint32_t(d), my_slot_bar);
+                    }
+                    slot_pending = true;
+                }
+            }
+        }
+        if (t == 0) {
+            if (has_cur)
+                s_chunk[(it + 2) % 3] = int64_t(claim);
+            if (out_tma)
+                ptx::bulk_wait_group_read<0>(); // the previous store has left the out stage
+        }
+        __syncthreads();
+
+        if (prev2 >= 0 || prev1 >= 0) { // uniform
+            const uint32_t region = uint32_t(t) * P::kPer * P::kInBytes;
+            if (prev2 >= 0) {
+                // Chunk prev2: its sequential run again (the same operations,
+                // so the same bits), plus the thread's block prefix, plus the
+                // carry added from the top level down.
+                Carry excl = Carry(0);
+                if (prev2 > 0) {
+                    bool first = true;
+                    for (int k = L.levels - 1; k >= 0; --k) {
+                        if (((prev2 >> (kRadixLog * k)) & 31) == 0)
+                            continue;
+                        excl = first ? s_level[k] : excl + s_level[k];
+                        first = false;
+                    }
+                }
+                const typename T::Split sc = T::split(excl);
+                Acc v[P::kPer];
+#pragma unroll
+                for (int w = 0; w < kWords; ++w) {
+                    if constexpr (P::kInBytes == 4) {
+                        v[w] = acc_of_bits<DT>(raw_prev2[w]);
+                    } else {
+                        v[2 * w] = acc_of_bits<DT>(raw_prev2[w] & 0xffffu);
+                        v[2 * w + 1] = acc_of_bits<DT>(raw_prev2[w] >> 16);
+                    }
+                }
+#pragma unroll
+                for (int j = 1; j < P::kPer; ++j)
+                    v[j] += v[j - 1];
+                const uint32_t oregion = uint32_t(t) * P::kPer * P::kOutBytes;
+                if constexpr (P::kOutBytes == 4) {
+#pragma unroll
+                    for (int q = 0; q < P::kPer / 4; ++q) {
+                        uint4 w;
+                        w.x = __float_as_uint(T::finish(sc, before_p2 + v[4 * q]));
+                        w.y = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 1]));
+                        w.z = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 2]));
+                        w.w = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 3]));
+                        ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < P::kPer / 2; ++q) {
+                        const unsigned long long a =
+                            static_cast<unsigned long long>(T::finish(sc, before_p2 + v[2 * q]));
+                        const unsigned long long b2 =
+                            static_cast<unsigned long long>(T::finish(sc, before_p2 + v[2 * q + 1]));
+                        ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
+                                    make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
+                    }
+                }
+            }
+            if (prev1 >= 0) {
+                // Chunk prev1 to registers: its stage takes chunk it+2 next
+                // iteration.
+                const uint32_t p1_addr = stage_addr + uint32_t((it + 2) % 3) * P::kInStage;
+#pragma unroll
+                for (int q = 0; q < kWords / 4; ++q) {
+                    const uint4 w = ptx::lds_v4(p1_addr + swz128(region + 16u * q));
+                    raw_prev2[4 * q] = w.x;
+                    raw_prev2[4 * q + 1] = w.y;
+                    raw_prev2[4 * q + 2] = w.z;
+                    raw_prev2[4 * q + 3] = w.w;
+                }
+            }
+            const bool store_tma = prev2 >= 0 && out_tma && prev2 < full_chunks;
+            if (store_tma)
+                ptx::fence_proxy_async_smem();
+            __syncthreads();
+            if (prev2 >= 0) {
+                if (store_tma) {
+                    if (t == 0) {
+                        ptx::tma_store_3d(&out_map, 0, 0, int32_t(prev2), out_addr);
+                        ptx::bulk_commit_group();
+                    }
+                } else {
+                    Out *out = static_cast<Out *>(dst);
+                    const int64_t pbase = prev2 * P::kChunk;
+#pragma unroll
+                    for (int k = 0; k < P::kPer; ++k) {
+                        const int e = t + k * kScanThreads;
+                        if (pbase + e < n)
+                            out[pbase + e] =
+                                *reinterpret_cast<const Out *>(out_stage + swz128(uint32_t(e * P::kOutBytes)));
+                    }
+                }
+            }
+        }
+        before_p2 = before_p1;
+        before_p1 = before;
+        prev2 = prev1;
+        prev1 = has_cur ? c : -1;
+    }
+    if (slot_pending && !ptx::mbar_wait_bounded(my_slot_bar, slot_phase, wait_limit_ns))
+        failed = true; // no copy is left in flight into this CTA's shared memory
+    if (t == 0 && out_tma)
+        ptx::bulk_wait_group<0>();
+    if (failed)
+        atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
+}
+
+// 0: single pass, carries used one chunk later (scan_deferred_kernel);
+// 1: three passes; 2: single pass, carries read at once (scan_onepass_kernel).
+std::atomic<int> g_scan_choice{0};
 
 template <int DT>
-optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, cudaStream_t stream)
+optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, int form, cudaStream_t stream)
 {
     using P = OnePass<DT>;
     DeviceInfo dev;
@@ -707,32 +1062,43 @@ optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, cudaSt
                                             CU_TENSOR_MAP_SWIZZLE_128B)) != OPTIGPU_OK)
         return st;
 
-    const void *fn = reinterpret_cast<const void *>(&scan_onepass_kernel<DT>);
-    static std::atomic<bool> attr_set[64];
-    if (dev.device < 0 || dev.device >= 64 || !attr_set[dev.device].load()) {
-        if ((st = check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P::kSmem),
+    const bool deferred = form == 0;
+    const void *fn = deferred ? reinterpret_cast<const void *>(&scan_deferred_kernel<DT>)
+                              : reinterpret_cast<const void *>(&scan_onepass_kernel<DT>);
+    const int smem = deferred ? P::kSmemDeferred : P::kSmem;
+    static std::atomic<bool> attr_set[2][64];
+    if (dev.device < 0 || dev.device >= 64 || !attr_set[deferred][dev.device].load()) {
+        if ((st = check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                              "cudaFuncSetAttribute(scan)")) != OPTIGPU_OK)
             return st;
         if (dev.device >= 0 && dev.device < 64)
-            attr_set[dev.device].store(true);
+            attr_set[deferred][dev.device].store(true);
     }
     int per_sm = 0;
-    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScanThreads, P::kSmem),
+    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScanThreads, smem),
                          "cudaOccupancyMaxActiveBlocksPerMultiprocessor(scan)")) != OPTIGPU_OK)
         return st;
     const int64_t grid = std::min<int64_t>(chunks, int64_t(std::max(per_sm, 1)) * dev.num_sms);
-    scan_onepass_kernel<DT><<<unsigned(grid), kScanThreads, P::kSmem, stream>>>(
-        in_map, out_map, src, dst, n, chunks, full_chunks, in_tma, out_tma,
-        reinterpret_cast<unsigned long long *>(b), reinterpret_cast<unsigned *>(b + off_groups),
-        reinterpret_cast<unsigned long long *>(b + off_blocks), L, wait_limit_ns(), dev.status_word);
+    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(b);
+    unsigned *groups = reinterpret_cast<unsigned *>(b + off_groups);
+    unsigned long long *blocks = reinterpret_cast<unsigned long long *>(b + off_blocks);
+    if (deferred)
+        scan_deferred_kernel<DT><<<unsigned(grid), kScanThreads, smem, stream>>>(
+            in_map, out_map, src, dst, n, chunks, full_chunks, in_tma, out_tma, ticket, groups, blocks, L,
+            wait_limit_ns(), dev.status_word);
+    else
+        scan_onepass_kernel<DT><<<unsigned(grid), kScanThreads, smem, stream>>>(
+            in_map, out_map, src, dst, n, chunks, full_chunks, in_tma, out_tma, ticket, groups, blocks, L,
+            wait_limit_ns(), dev.status_word);
     return check_cuda(cudaGetLastError(), "launch scan (single pass)");
 }
 
 template <int DT>
 optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t stream)
 {
-    if (g_scan_choice.load() == 0)
-        return launch_scan_onepass<DT>(src, dst, n, stream);
+    const int choice = g_scan_choice.load();
+    if (choice != 1)
+        return launch_scan_onepass<DT>(src, dst, n, choice, stream);
     using T = ScanTraits<DT>;
     using P = typename std::conditional<DT == OPTIGPU_INT32, long long, double>::type;
     DeviceInfo dev;
@@ -758,10 +1124,13 @@ optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t s
 
 } // namespace
 
-int scan_num_configs() { return 2; }
+int scan_num_configs() { return 3; }
 const char *scan_config_name(int c)
 {
-    return c == 0 ? "scan single pass (dyadic carries)" : c == 1 ? "scan three passes" : nullptr;
+    return c == 0   ? "scan single pass (carries used one chunk later)"
+           : c == 1 ? "scan three passes"
+           : c == 2 ? "scan single pass (carries read at once)"
+                    : nullptr;
 }
 int scan_selected() { return g_scan_choice.load(); }
 void scan_select(int c) { g_scan_choice.store(c); }

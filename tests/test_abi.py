@@ -188,7 +188,8 @@ def test_tune_cache_keeps_the_scan_form(lib, tmp_path):
     assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
     assert lib.optigpu_tune_load(path) == N.OK
     assert lib.optigpu_tune_selected(N.OP_SCAN, 0) == 1
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 2) == N.ERR_INVALID_ARG
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 2) == N.OK
+    assert lib.optigpu_tune_select(N.OP_SCAN, 0, lib.optigpu_tune_num_configs(N.OP_SCAN, 0)) == N.ERR_INVALID_ARG
     assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
 
 

@@ -132,7 +132,7 @@ def _abs_bits(a, dtype):
     return np.abs(a)
 
 
-@pytest.fixture(params=[0, 1], ids=["single_pass", "three_pass"])
+@pytest.fixture(params=[0, 1, 2], ids=["single_pass", "three_pass", "single_pass_carries_at_once"])
 def scan_config(request):
     prev = api.tune_selected("scan", torch.float32)
     api.tune_select("scan", torch.float32, request.param)
@@ -214,13 +214,33 @@ def test_scan_infinities_and_nan(n, scan_config):
 
 def test_scan_autotune_selects_a_form():
     best, name, ms = api.autotune("scan", torch.float32, 1 << 12, 1 << 12, reps=3)
-    assert best in (0, 1) and ms > 0 and name == api.tune_configs("scan", torch.float32)[best]
+    forms = api.tune_configs("scan", torch.float32)
+    assert 0 <= best < len(forms) and ms > 0 and name == forms[best]
     assert api.tune_selected("scan", torch.float32) == best
     a = workloads.vector(100003, "float32", seed=12)
     got = api.scan(to_device(a, "float32")).cpu().numpy().astype(np.float64)
     scale = oracle.scan(np.abs(a), "float32")
     assert (np.abs(got - oracle.scan(a, "float32")) <= 1e-6 * scale + 1e-30).all()
     api.tune_select("scan", torch.float32, 0)
+
+
+@pytest.mark.parametrize("dtype,n", [("float32", (1 << 24) + 77), ("int32", (1 << 23) + 5),
+                                     ("bfloat16", 1 << 22), ("float16", 4096 * 40 + 1)])
+def test_scan_single_pass_forms_give_the_same_bits(dtype, n):
+    # The two single-pass forms (configurations 0 and 2) form every output by
+    # the same operations in the same order; only the moment the carry is
+    # read differs.
+    a = workloads.vector(n, dtype, seed=n + 31)
+    d = to_device(a, dtype)
+    prev = api.tune_selected("scan", torch.float32)
+    try:
+        api.tune_select("scan", torch.float32, 0)
+        first = api.scan(d).cpu().numpy()
+        api.tune_select("scan", torch.float32, 2)
+        second = api.scan(d).cpu().numpy()
+    finally:
+        api.tune_select("scan", torch.float32, prev)
+    assert first.tobytes() == second.tobytes()
 
 
 def test_scan_repeatable_many_chunks(scan_config):
