@@ -10,6 +10,7 @@
 // whatever the order, so the result is bit-exact.  Histograms with more bins
 // than fit in shared memory count directly with global atomics.
 #include <algorithm>
+#include <climits>
 
 #include "internal.h"
 
@@ -35,13 +36,33 @@ struct BinRule {
     }
 };
 
-template <bool SMEM>
-__global__ void __launch_bounds__(kHistThreads)
-histogram_kernel(const int32_t *__restrict__ src, int64_t n, BinRule rule, unsigned long long *counts, int vec_ok)
+// The same rule in 32-bit arithmetic, valid when lo is an int32 and
+// width < 2^32: for x >= lo, x - lo lies in [0, 2^32) and is exact as an
+// unsigned 32-bit value.
+struct BinRule32 {
+    int32_t lo;
+    uint32_t width;
+    uint32_t nbins;
+    int shift;
+
+    __device__ __forceinline__ int64_t bin(int32_t x) const
+    {
+        if (x < lo)
+            return -1;
+        const uint32_t d = uint32_t(x) - uint32_t(lo);
+        const uint32_t b = shift >= 0 ? (d >> shift) : d / width;
+        return b < nbins ? int64_t(b) : -1;
+    }
+};
+
+template <bool SMEM, typename Rule>
+__global__ void __launch_bounds__(kHistThreads, 3)
+histogram_kernel(const int32_t *__restrict__ src, int64_t n, Rule rule, int64_t nbins, unsigned long long *counts,
+                 int vec_ok)
 {
     extern __shared__ unsigned int local[];
     if (SMEM) {
-        for (int64_t b = threadIdx.x; b < rule.nbins; b += kHistThreads)
+        for (int64_t b = threadIdx.x; b < nbins; b += kHistThreads)
             local[b] = 0u;
         __syncthreads();
     }
@@ -90,7 +111,7 @@ histogram_kernel(const int32_t *__restrict__ src, int64_t n, BinRule rule, unsig
     }
     if (SMEM) {
         __syncthreads();
-        for (int64_t b = threadIdx.x; b < rule.nbins; b += kHistThreads)
+        for (int64_t b = threadIdx.x; b < nbins; b += kHistThreads)
             if (local[b])
                 atomicAdd(&counts[b], static_cast<unsigned long long>(local[b]));
     }
@@ -127,14 +148,32 @@ extern "C" optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, i
     }
     const bool smem = nbins <= kSmemBins;
     const size_t smem_bytes = smem ? sizeof(unsigned) * size_t(nbins) : 0;
-    const int per_sm = smem ? std::max(1, int((200u * 1024u) / std::max<size_t>(smem_bytes + 1024, 16384))) : 4;
+    const bool narrow = lo >= INT32_MIN && lo <= INT32_MAX && width < (int64_t(1) << 32);
+    const void *fn = narrow ? (smem ? reinterpret_cast<const void *>(&histogram_kernel<true, BinRule32>)
+                                    : reinterpret_cast<const void *>(&histogram_kernel<false, BinRule32>))
+                            : (smem ? reinterpret_cast<const void *>(&histogram_kernel<true, BinRule>)
+                                    : reinterpret_cast<const void *>(&histogram_kernel<false, BinRule>));
+    // One wave: as many CTAs as are resident at once (every CTA walks the
+    // input grid-stride, so a second wave would run alone at the end).
+    int per_sm = 0;
+    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kHistThreads, smem_bytes),
+                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(histogram)")) != OPTIGPU_OK)
+        return st;
     const int64_t want = (n + int64_t(kHistThreads) * 16 - 1) / (int64_t(kHistThreads) * 16);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::min(per_sm, 4)) * dev.num_sms));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(per_sm, 1)) * dev.num_sms));
     const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
     auto *c = reinterpret_cast<unsigned long long *>(counts);
-    if (smem)
-        histogram_kernel<true><<<unsigned(grid), kHistThreads, smem_bytes, s>>>(src, n, rule, c, vec_ok);
-    else
-        histogram_kernel<false><<<unsigned(grid), kHistThreads, 0, s>>>(src, n, rule, c, vec_ok);
+    const int64_t nb = nbins;
+    if (narrow) {
+        const BinRule32 r32{int32_t(lo), uint32_t(width), uint32_t(nbins), rule.shift};
+        if (smem)
+            histogram_kernel<true><<<unsigned(grid), kHistThreads, smem_bytes, s>>>(src, n, r32, nb, c, vec_ok);
+        else
+            histogram_kernel<false><<<unsigned(grid), kHistThreads, 0, s>>>(src, n, r32, nb, c, vec_ok);
+    } else if (smem) {
+        histogram_kernel<true><<<unsigned(grid), kHistThreads, smem_bytes, s>>>(src, n, rule, nb, c, vec_ok);
+    } else {
+        histogram_kernel<false><<<unsigned(grid), kHistThreads, 0, s>>>(src, n, rule, nb, c, vec_ok);
+    }
     return check_cuda(cudaGetLastError(), "launch histogram");
 }

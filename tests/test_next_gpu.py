@@ -253,7 +253,10 @@ def test_scan_repeatable_many_chunks(scan_config):
 
 
 @pytest.mark.parametrize("lo,width,nbins", [(0, 1, 100), (-50, 7, 29), (-1000, 1, 2001), (0, 16, 4096),
-                                            (-2**31, 2**24, 256), (5, 3, 20000), (0, 1, 1)])
+                                            (-2**31, 2**24, 256), (5, 3, 20000), (0, 1, 1),
+                                            # 64-bit bin rule: lo outside int32, or width >= 2^32
+                                            (-2**35, 2**24, 4096), (-2**33, 3 * 2**30 + 7, 8),
+                                            (-2**32, 2**32, 3), (2**31, 1, 64), (-2**34, 2**20, 20000)])
 @pytest.mark.parametrize("n", [0, 1, 1000, 123457, 1 << 22])
 def test_histogram_matches_oracle(lo, width, nbins, n):
     rng = np.random.default_rng(n + nbins)
