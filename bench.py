@@ -51,8 +51,8 @@ METRIC = "transpose/reduce HBM GB/s (% of GB300 peak)"
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
 # TRANSPOSE_SOURCES below).
-NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073773312 + 1027839232,
-                         "src_sha256": "48247ea6bce93014c160bbc09323379cc51639007543f4bbc490bd5655484b65"}
+NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073798400 + 1028149504,
+                         "src_sha256": "316dfdfc032354f5230c8752f3d1cee90c213ae402953e4e2f9300e8775f75dc"}
 
 
 def _peaks():
