@@ -150,6 +150,17 @@ def pin_histogram(h):
     assert (h(r, 0, 10, 100) == 10).all()
     assert h(np.full(5, -1, dtype=np.int32), 0, 1, 3).sum() == 0
     assert h(np.array([2**31 - 1, -2**31], dtype=np.int32), -2**31, 2**31, 2).tolist() == [1, 1]
+    # lo outside int32 and widths of 2^32 and more: the bin of x is (x - lo) // width in exact
+    # integer arithmetic.
+    full = rng.integers(-2**31, 2**31, size=20000, dtype=np.int64).astype(np.int32)
+    for lo, w, nb in ((-2**35, 2**24, 4096), (-2**33, 3 * 2**30 + 7, 8), (-2**32, 2**32, 3),
+                      (-2**34, 2**20, 20000)):
+        d = full.astype(np.int64) - lo
+        want = np.bincount(d // w, minlength=nb)[:nb]
+        assert np.array_equal(h(full, lo, w, nb), want), (lo, w, nb)
+    assert h(full, 2**31, 1, 64).sum() == 0                 # every int32 lies below lo
+    # x - lo lies in [2^31, 3 * 2^31): negative values in bin 0, the rest in bin 1.
+    assert h(full, -2**32, 2**32, 3).tolist() == [int((full < 0).sum()), int((full >= 0).sum()), 0]
 
 
 def test_oracle_histogram_pins():
