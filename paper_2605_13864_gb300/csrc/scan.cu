@@ -343,6 +343,7 @@ struct OnePass {
     // rate follows the number of resident CTAs, not the bytes per CTA.)
     static constexpr int kPer = kPerThread;
     static constexpr int kChunk = kScanThreads * kPer; // 4096
+    static constexpr int kWords = kPer * kInBytes / 4;  // raw 32-bit words per thread
     static constexpr int kInStage = kChunk * kInBytes;   // 16 KiB or 8 KiB
     static constexpr int kOutStage = kChunk * kOutBytes; // 16 KiB or 32 KiB
     static constexpr int kSmem = 2 * kInStage + kOutStage + 1024;
@@ -367,6 +368,159 @@ __device__ __forceinline__ typename ScanTraits<DT>::Acc acc_of_bits(uint32_t w)
         return __uint_as_float(w << 16);
     else
         return __half2float(__ushort_as_half(static_cast<unsigned short>(w & 0xffffu)));
+}
+
+// Chunk c staged from plain loads (the ragged last chunk, or a source that
+// is not 16-byte aligned) in the swizzled layout a TMA load gives; elements
+// past n are zero.
+template <int DT>
+__device__ __forceinline__ void stage_chunk_plain(unsigned char *in_ptr, const void *src, int64_t n, int64_t base)
+{
+    using P = OnePass<DT>;
+#pragma unroll
+    for (int k = 0; k < P::kPer; ++k) {
+        const int e = int(threadIdx.x) + k * kScanThreads;
+        const int64_t i = base + e;
+        const uint32_t off = swz128(uint32_t(e * P::kInBytes));
+        if constexpr (P::kInBytes == 4)
+            *reinterpret_cast<uint32_t *>(in_ptr + off) = i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
+        else
+            *reinterpret_cast<uint16_t *>(in_ptr + off) =
+                i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
+    }
+}
+
+// Thread t's raw words: elements kPer t .. kPer t + kPer - 1 of the staged
+// chunk.
+template <int DT>
+__device__ __forceinline__ void load_raw(uint32_t in_addr, uint32_t (&raw)[OnePass<DT>::kWords])
+{
+    using P = OnePass<DT>;
+    const uint32_t region = uint32_t(threadIdx.x) * P::kPer * P::kInBytes;
+#pragma unroll
+    for (int q = 0; q < P::kWords / 4; ++q) {
+        const uint4 w = ptx::lds_v4(in_addr + swz128(region + 16u * q));
+        raw[4 * q] = w.x;
+        raw[4 * q + 1] = w.y;
+        raw[4 * q + 2] = w.z;
+        raw[4 * q + 3] = w.w;
+    }
+}
+
+// Sequential sum of the thread's elements, in element order.
+template <int DT>
+__device__ __forceinline__ typename ScanTraits<DT>::Acc thread_run(const uint32_t (&raw)[OnePass<DT>::kWords])
+{
+    using Acc = typename ScanTraits<DT>::Acc;
+    Acc run = Acc(0);
+#pragma unroll
+    for (int w = 0; w < OnePass<DT>::kWords; ++w) {
+        if constexpr (OnePass<DT>::kInBytes == 4) {
+            run += acc_of_bits<DT>(raw[w]);
+        } else {
+            run += acc_of_bits<DT>(raw[w] & 0xffffu);
+            run += acc_of_bits<DT>(raw[w] >> 16);
+        }
+    }
+    return run;
+}
+
+// Publishes B(0, c) = total, then forms every block chunk c completes as the
+// 32nd arrival of its group.  Called by one whole warp; false in a lane whose
+// wait for a child gave up.
+template <typename Carry>
+__device__ __forceinline__ bool publish_and_form(unsigned long long *blocks, unsigned *groups, const ScanLevels &L,
+                                                 int64_t c, Carry total, uint64_t wait_limit_ns)
+{
+    const int lane = int(threadIdx.x) & 31;
+    bool ok = true;
+    if (lane == 0)
+        publish_block<Carry>(blocks + 2 * (L.block_off[0] + uint64_t(c)), total);
+    int64_t j = c;
+    for (int k = 0; k + 1 < L.levels; ++k) {
+        const int64_t parent = j >> kRadixLog;
+        if (((parent + 1) << kRadixLog) > L.count[k])
+            break; // an incomplete group is never needed
+        unsigned last = 0;
+        if (lane == 0)
+            last = atomicAdd(groups + L.group_off[k] + uint64_t(parent), 1u) == 31u;
+        if (!__shfl_sync(0xffffffffu, last, 0))
+            break; // later arrivals form it
+        Carry x;
+        if (!wait_block<Carry>(blocks + 2 * (L.block_off[k] + uint64_t((parent << kRadixLog) + lane)), x,
+                               wait_limit_ns))
+            ok = false;
+#pragma unroll
+        for (int d = 16; d; d >>= 1)
+            x += __shfl_xor_sync(0xffffffffu, x, d);
+        if (lane == 0)
+            publish_block<Carry>(blocks + 2 * (L.block_off[k + 1] + uint64_t(parent)), x);
+        j = parent;
+    }
+    return ok;
+}
+
+// The outputs of one chunk into the swizzled out stage: the thread's
+// sequential run again (the same operations, so the same bits), plus its
+// block prefix, plus the carry.
+template <int DT>
+__device__ __forceinline__ void finish_chunk(const uint32_t (&raw)[OnePass<DT>::kWords],
+                                             typename ScanTraits<DT>::Acc before, typename ScanTraits<DT>::Split sc,
+                                             uint32_t out_addr)
+{
+    using P = OnePass<DT>;
+    using T = ScanTraits<DT>;
+    using Acc = typename T::Acc;
+    Acc v[P::kPer];
+#pragma unroll
+    for (int w = 0; w < P::kWords; ++w) {
+        if constexpr (P::kInBytes == 4) {
+            v[w] = acc_of_bits<DT>(raw[w]);
+        } else {
+            v[2 * w] = acc_of_bits<DT>(raw[w] & 0xffffu);
+            v[2 * w + 1] = acc_of_bits<DT>(raw[w] >> 16);
+        }
+    }
+#pragma unroll
+    for (int j = 1; j < P::kPer; ++j)
+        v[j] += v[j - 1];
+    const uint32_t oregion = uint32_t(threadIdx.x) * P::kPer * P::kOutBytes;
+    if constexpr (P::kOutBytes == 4) {
+#pragma unroll
+        for (int q = 0; q < P::kPer / 4; ++q) {
+            uint4 w;
+            w.x = __float_as_uint(T::finish(sc, before + v[4 * q]));
+            w.y = __float_as_uint(T::finish(sc, before + v[4 * q + 1]));
+            w.z = __float_as_uint(T::finish(sc, before + v[4 * q + 2]));
+            w.w = __float_as_uint(T::finish(sc, before + v[4 * q + 3]));
+            ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < P::kPer / 2; ++q) {
+            const unsigned long long a = static_cast<unsigned long long>(T::finish(sc, before + v[2 * q]));
+            const unsigned long long b2 = static_cast<unsigned long long>(T::finish(sc, before + v[2 * q + 1]));
+            ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
+                        make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
+        }
+    }
+}
+
+// A finished chunk from the out stage to dst with plain coalesced stores (the
+// ragged last chunk, or a destination that is not 16-byte aligned).
+template <int DT>
+__device__ __forceinline__ void store_chunk_plain(void *dst, int64_t n, int64_t chunk, const unsigned char *out_stage)
+{
+    using P = OnePass<DT>;
+    using Out = typename ScanTraits<DT>::Out;
+    Out *out = static_cast<Out *>(dst);
+    const int64_t pbase = chunk * P::kChunk;
+#pragma unroll
+    for (int k = 0; k < P::kPer; ++k) {
+        const int e = int(threadIdx.x) + k * kScanThreads;
+        if (pbase + e < n)
+            out[pbase + e] = *reinterpret_cast<const Out *>(out_stage + swz128(uint32_t(e * P::kOutBytes)));
+    }
 }
 
 // Single-pass scan.  A persistent grid claims chunks in order through an
@@ -396,7 +550,7 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
     using Acc = typename T::Acc;
     using Carry = typename T::Carry;
     using Out = typename T::Out;
-    constexpr int kWords = P::kPer * P::kInBytes / 4; // raw 32-bit words per thread
+    constexpr int kWords = P::kWords;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ Acc warp_tot[kScanThreads / 32];
@@ -461,19 +615,7 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
                     break;
                 }
             } else {
-                unsigned char *in_ptr = stage + buf * P::kInStage;
-#pragma unroll
-                for (int k = 0; k < P::kPer; ++k) {
-                    const int e = t + k * kScanThreads;
-                    const int64_t i = base + e;
-                    const uint32_t off = swz128(uint32_t(e * P::kInBytes));
-                    if constexpr (P::kInBytes == 4)
-                        *reinterpret_cast<uint32_t *>(in_ptr + off) =
-                            i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
-                    else
-                        *reinterpret_cast<uint16_t *>(in_ptr + off) =
-                            i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
-                }
+                stage_chunk_plain<DT>(stage + buf * P::kInStage, src, n, base);
                 __syncthreads();
             }
             if (t == 0) {
@@ -489,55 +631,14 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
                 }
                 claim = cn < num_chunks ? atomicAdd(ticket, 1ull) : (unsigned long long)num_chunks;
             }
-            // Thread t scans elements 16 t .. 16 t + 15 of the chunk.
-            const uint32_t region = uint32_t(t) * P::kPer * P::kInBytes;
-#pragma unroll
-            for (int q = 0; q < kWords / 4; ++q) {
-                const uint4 w = ptx::lds_v4(in_addr + swz128(region + 16u * q));
-                raw[4 * q] = w.x;
-                raw[4 * q + 1] = w.y;
-                raw[4 * q + 2] = w.z;
-                raw[4 * q + 3] = w.w;
-            }
-            Acc run = Acc(0);
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) {
-                if constexpr (P::kInBytes == 4) {
-                    run += acc_of_bits<DT>(raw[w]);
-                } else {
-                    run += acc_of_bits<DT>(raw[w] & 0xffffu);
-                    run += acc_of_bits<DT>(raw[w] >> 16);
-                }
-            }
+            load_raw<DT>(in_addr, raw);
+            const Acc run = thread_run<DT>(raw);
             Acc total;
             before = block_exclusive_scan<Acc>(run, warp_tot, &total);
-            if (warp == 1) {
-                // Publish B(0, c), then form every block this chunk completes
-                // as the 32nd arrival of its group.
-                if (lane == 0)
-                    publish_block<Carry>(blocks + 2 * (L.block_off[0] + uint64_t(c)), Carry(total));
-                int64_t j = c;
-                for (int k = 0; k + 1 < L.levels; ++k) {
-                    const int64_t parent = j >> kRadixLog;
-                    if (((parent + 1) << kRadixLog) > L.count[k])
-                        break; // an incomplete group is never needed
-                    unsigned last = 0;
-                    if (lane == 0)
-                        last = atomicAdd(groups + L.group_off[k] + uint64_t(parent), 1u) == 31u;
-                    if (!__shfl_sync(0xffffffffu, last, 0))
-                        break; // later arrivals form it
-                    Carry x;
-                    if (!wait_block<Carry>(blocks + 2 * (L.block_off[k] + uint64_t((parent << kRadixLog) + lane)), x,
-                                           wait_limit_ns))
-                        failed = true;
-#pragma unroll
-                    for (int d = 16; d; d >>= 1)
-                        x += __shfl_xor_sync(0xffffffffu, x, d);
-                    if (lane == 0)
-                        publish_block<Carry>(blocks + 2 * (L.block_off[k + 1] + uint64_t(parent)), x);
-                    j = parent;
-                }
-            }
+            // Warp 1 publishes the total of chunk c and forms the blocks it
+            // completes, beside warp 0's carry below.
+            if (warp == 1 && !publish_and_form<Carry>(blocks, groups, L, c, Carry(total), wait_limit_ns))
+                failed = true;
         }
 
         const bool pending = prev >= 0;
@@ -593,42 +694,7 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
             // Outputs of the pending chunk: its sequential run again (the
             // same operations, so the same bits), plus the thread's block
             // prefix, plus the carry.
-            const typename T::Split sc = T::split(s_excl);
-            Acc v[P::kPer];
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) {
-                if constexpr (P::kInBytes == 4) {
-                    v[w] = acc_of_bits<DT>(raw_prev[w]);
-                } else {
-                    v[2 * w] = acc_of_bits<DT>(raw_prev[w] & 0xffffu);
-                    v[2 * w + 1] = acc_of_bits<DT>(raw_prev[w] >> 16);
-                }
-            }
-#pragma unroll
-            for (int j = 1; j < P::kPer; ++j)
-                v[j] += v[j - 1];
-            const uint32_t oregion = uint32_t(t) * P::kPer * P::kOutBytes;
-            if constexpr (P::kOutBytes == 4) {
-#pragma unroll
-                for (int q = 0; q < P::kPer / 4; ++q) {
-                    uint4 w;
-                    w.x = __float_as_uint(T::finish(sc, before_prev + v[4 * q]));
-                    w.y = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 1]));
-                    w.z = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 2]));
-                    w.w = __float_as_uint(T::finish(sc, before_prev + v[4 * q + 3]));
-                    ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < P::kPer / 2; ++q) {
-                    const unsigned long long a =
-                        static_cast<unsigned long long>(T::finish(sc, before_prev + v[2 * q]));
-                    const unsigned long long b2 =
-                        static_cast<unsigned long long>(T::finish(sc, before_prev + v[2 * q + 1]));
-                    ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
-                                make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
-                }
-            }
+            finish_chunk<DT>(raw_prev, before_prev, T::split(s_excl), out_addr);
             const bool store_tma = out_tma && prev < full_chunks;
             if (store_tma)
                 ptx::fence_proxy_async_smem();
@@ -639,14 +705,7 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
                     ptx::bulk_commit_group();
                 }
             } else {
-                Out *out = static_cast<Out *>(dst);
-                const int64_t pbase = prev * P::kChunk;
-#pragma unroll
-                for (int k = 0; k < P::kPer; ++k) {
-                    const int e = t + k * kScanThreads;
-                    if (pbase + e < n)
-                        out[pbase + e] = *reinterpret_cast<const Out *>(out_stage + swz128(uint32_t(e * P::kOutBytes)));
-                }
+                store_chunk_plain<DT>(dst, n, prev, out_stage);
             }
         }
         if (!has_cur)
@@ -694,7 +753,7 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
     using Acc = typename T::Acc;
     using Carry = typename T::Carry;
     using Out = typename T::Out;
-    constexpr int kWords = P::kPer * P::kInBytes / 4; // raw 32-bit words per thread
+    constexpr int kWords = P::kWords;
     constexpr int kPubWarp = kScanThreads / 32 - 1;
     static_assert(kMaxLevels <= kPubWarp, "one warp per carry level, one to publish");
     extern __shared__ unsigned char smem_raw[];
@@ -769,19 +828,7 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
                     break;
                 }
             } else {
-                unsigned char *in_ptr = stage + sidx * P::kInStage;
-#pragma unroll
-                for (int k = 0; k < P::kPer; ++k) {
-                    const int e = t + k * kScanThreads;
-                    const int64_t i = base + e;
-                    const uint32_t off = swz128(uint32_t(e * P::kInBytes));
-                    if constexpr (P::kInBytes == 4)
-                        *reinterpret_cast<uint32_t *>(in_ptr + off) =
-                            i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
-                    else
-                        *reinterpret_cast<uint16_t *>(in_ptr + off) =
-                            i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
-                }
+                stage_chunk_plain<DT>(stage + sidx * P::kInStage, src, n, base);
                 __syncthreads();
             }
             if (t == 0) {
@@ -798,55 +845,13 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
                 claim = cn < num_chunks ? atomicAdd(ticket, 1ull) : (unsigned long long)num_chunks;
             }
             // Thread t scans elements 16 t .. 16 t + 15 of the chunk.
-            const uint32_t region = uint32_t(t) * P::kPer * P::kInBytes;
             uint32_t raw[kWords];
-#pragma unroll
-            for (int q = 0; q < kWords / 4; ++q) {
-                const uint4 w = ptx::lds_v4(in_addr + swz128(region + 16u * q));
-                raw[4 * q] = w.x;
-                raw[4 * q + 1] = w.y;
-                raw[4 * q + 2] = w.z;
-                raw[4 * q + 3] = w.w;
-            }
-            Acc run = Acc(0);
-#pragma unroll
-            for (int w = 0; w < kWords; ++w) {
-                if constexpr (P::kInBytes == 4) {
-                    run += acc_of_bits<DT>(raw[w]);
-                } else {
-                    run += acc_of_bits<DT>(raw[w] & 0xffffu);
-                    run += acc_of_bits<DT>(raw[w] >> 16);
-                }
-            }
+            load_raw<DT>(in_addr, raw);
+            const Acc run = thread_run<DT>(raw);
             Acc total;
             before = block_exclusive_scan<Acc>(run, warp_tot, &total);
-            if (warp == kPubWarp) {
-                // Publish B(0, c), then form every block this chunk completes
-                // as the 32nd arrival of its group.
-                if (lane == 0)
-                    publish_block<Carry>(blocks + 2 * (L.block_off[0] + uint64_t(c)), Carry(total));
-                int64_t j = c;
-                for (int k = 0; k + 1 < L.levels; ++k) {
-                    const int64_t parent = j >> kRadixLog;
-                    if (((parent + 1) << kRadixLog) > L.count[k])
-                        break; // an incomplete group is never needed
-                    unsigned last = 0;
-                    if (lane == 0)
-                        last = atomicAdd(groups + L.group_off[k] + uint64_t(parent), 1u) == 31u;
-                    if (!__shfl_sync(0xffffffffu, last, 0))
-                        break; // later arrivals form it
-                    Carry x;
-                    if (!wait_block<Carry>(blocks + 2 * (L.block_off[k] + uint64_t((parent << kRadixLog) + lane)), x,
-                                           wait_limit_ns))
-                        failed = true;
-#pragma unroll
-                    for (int d = 16; d; d >>= 1)
-                        x += __shfl_xor_sync(0xffffffffu, x, d);
-                    if (lane == 0)
-                        publish_block<Carry>(blocks + 2 * (L.block_off[k + 1] + uint64_t(parent)), x);
-                    j = parent;
-                }
-            }
+            if (warp == kPubWarp && !publish_and_form<Carry>(blocks, groups, L, c, Carry(total), wait_limit_ns))
+                failed = true;
         }
 
         if (warp < L.levels) {
@@ -901,7 +906,6 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
         __syncthreads();
 
         if (prev2 >= 0 || prev1 >= 0) { // uniform
-            const uint32_t region = uint32_t(t) * P::kPer * P::kInBytes;
             if (prev2 >= 0) {
                 // Chunk prev2: its sequential run again (the same operations,
                 // so the same bits), plus the thread's block prefix, plus the
@@ -916,55 +920,12 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
                         first = false;
                     }
                 }
-                const typename T::Split sc = T::split(excl);
-                Acc v[P::kPer];
-#pragma unroll
-                for (int w = 0; w < kWords; ++w) {
-                    if constexpr (P::kInBytes == 4) {
-                        v[w] = acc_of_bits<DT>(raw_prev2[w]);
-                    } else {
-                        v[2 * w] = acc_of_bits<DT>(raw_prev2[w] & 0xffffu);
-                        v[2 * w + 1] = acc_of_bits<DT>(raw_prev2[w] >> 16);
-                    }
-                }
-#pragma unroll
-                for (int j = 1; j < P::kPer; ++j)
-                    v[j] += v[j - 1];
-                const uint32_t oregion = uint32_t(t) * P::kPer * P::kOutBytes;
-                if constexpr (P::kOutBytes == 4) {
-#pragma unroll
-                    for (int q = 0; q < P::kPer / 4; ++q) {
-                        uint4 w;
-                        w.x = __float_as_uint(T::finish(sc, before_p2 + v[4 * q]));
-                        w.y = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 1]));
-                        w.z = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 2]));
-                        w.w = __float_as_uint(T::finish(sc, before_p2 + v[4 * q + 3]));
-                        ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < P::kPer / 2; ++q) {
-                        const unsigned long long a =
-                            static_cast<unsigned long long>(T::finish(sc, before_p2 + v[2 * q]));
-                        const unsigned long long b2 =
-                            static_cast<unsigned long long>(T::finish(sc, before_p2 + v[2 * q + 1]));
-                        ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
-                                    make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
-                    }
-                }
+                finish_chunk<DT>(raw_prev2, before_p2, T::split(excl), out_addr);
             }
             if (prev1 >= 0) {
                 // Chunk prev1 to registers: its stage takes chunk it+2 next
                 // iteration.
-                const uint32_t p1_addr = stage_addr + uint32_t((it + 2) % 3) * P::kInStage;
-#pragma unroll
-                for (int q = 0; q < kWords / 4; ++q) {
-                    const uint4 w = ptx::lds_v4(p1_addr + swz128(region + 16u * q));
-                    raw_prev2[4 * q] = w.x;
-                    raw_prev2[4 * q + 1] = w.y;
-                    raw_prev2[4 * q + 2] = w.z;
-                    raw_prev2[4 * q + 3] = w.w;
-                }
+                load_raw<DT>(stage_addr + uint32_t((it + 2) % 3) * P::kInStage, raw_prev2);
             }
             const bool store_tma = prev2 >= 0 && out_tma && prev2 < full_chunks;
             if (store_tma)
@@ -977,15 +938,7 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
                         ptx::bulk_commit_group();
                     }
                 } else {
-                    Out *out = static_cast<Out *>(dst);
-                    const int64_t pbase = prev2 * P::kChunk;
-#pragma unroll
-                    for (int k = 0; k < P::kPer; ++k) {
-                        const int e = t + k * kScanThreads;
-                        if (pbase + e < n)
-                            out[pbase + e] =
-                                *reinterpret_cast<const Out *>(out_stage + swz128(uint32_t(e * P::kOutBytes)));
-                    }
+                    store_chunk_plain<DT>(dst, n, prev2, out_stage);
                 }
             }
         }
