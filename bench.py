@@ -427,14 +427,77 @@ def measure_precision():
     return res
 
 
+# Table 7.4 of the thesis: effective bandwidth (GB/s) at its own sizes, a
+# 4096x4096 fp32 transpose and a 16M-element sum, on an RTX 5060.  Context
+# for the paper-size line below; another machine's figures, not a target.
+TABLE_7_4_GBS = {"transpose_generated": 297.7, "transpose_no_bank_conflicts": 340.6,
+                 "reduce_generated": 297.9, "reduce3": 349.4, "reduce6": 376.8}
+
+
+def measure_paper_sizes(reps: int = 50):
+    """The thesis's own benchmark sizes (Table 7.4): a 4096x4096 fp32
+    transpose (TMA kernel and the padded tile32 baseline) and a 2^24 fp32 sum.
+    Each is timed twice with CUDA events around single calls, median of
+    `reps`: back to back (inputs left in L2, which holds both 64 MiB
+    matrices) and with L2 flushed before every call (a write of twice the L2
+    size, queued between the calls)."""
+    import statistics
+
+    import torch
+    from paper_2605_13864_gb300 import api
+
+    peak, _ = _peaks()
+    g = torch.Generator(device="cuda").manual_seed(1)
+    side, n = 4096, 1 << 24
+    a = torch.randn(side, side, device="cuda", generator=g)
+    b = torch.empty(side, side, device="cuda")
+    v = torch.randn(n, device="cuda", generator=g)
+    out = torch.empty((), dtype=torch.float64, device="cuda")
+    l2 = int(getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 0)) or (128 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def med_ms(fn, flushed):
+        # Every call is bracketed by its own events, all enqueued before one
+        # synchronize, so host-side call overhead overlaps queued GPU work
+        # instead of showing up between the events.
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            if flushed:
+                flush.fill_(1.0)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    res = {}
+    for name, fn, nbytes in (
+            ("transpose_4096_fp32_tma", lambda: api.transpose(a, out=b, kernel="tma"), 2 * side * side * 4),
+            ("transpose_4096_fp32_tile32", lambda: api.transpose(a, out=b, kernel="tile32"), 2 * side * side * 4),
+            ("sum_2p24_fp32", lambda: api.reduce_sum(v, out=out), n * 4)):
+        entry = {"algorithmic_bytes": nbytes}
+        for tag, flushed in (("l2_resident", False), ("l2_flushed", True)):
+            ms = med_ms(fn, flushed)
+            gbs = nbytes / ms / 1e6
+            entry[tag] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 4)}
+        res[name] = entry
+    res["table_7_4_gbs_rtx5060"] = TABLE_7_4_GBS
+    del a, b, v, flush
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_next(reps: int = 10):
     """The neighbouring problems at roofline scale, CUDA-event timed:
     batched transpose (64 x 2048^2 fp32), in-place transpose (16384^2 fp32),
     segmented sums (2^28 fp32 in 16384 segments), inclusive scans (2^28 int32
     -> int64, fp32 -> fp32 and bf16 -> fp32, each tuner form) and the int32
-    histogram (2^28 values,
-    4096 bins).  Bytes follow the same convention: every input byte read
-    once plus every output byte written once."""
+    histogram (2^28 values, 4096 bins).  Bytes follow the same convention:
+    every input byte read once plus every output byte written once."""
     import torch
     from paper_2605_13864_gb300 import api
 
@@ -652,6 +715,8 @@ def run_gpu(args):
             line["precision"] = measure_precision()
         if not args.no_next:
             line["next"] = measure_next()
+        if not args.no_paper_sizes:
+            line["paper_sizes"] = measure_paper_sizes()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -749,6 +814,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--no-paper-sizes", action="store_true")
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, "
