@@ -267,11 +267,15 @@ struct ScanLevels {
     uint64_t group_off[kMaxLevels]; // first group counter of level k (k < levels-1)
 };
 
-// A published block sum is two 64-bit words, each a nonzero tag over one
-// 32-bit half of the value, so a reader that sees both tags has the whole
-// value: no fence orders the halves (the slots start zeroed every launch).
-// Both words move in one 16-byte GPU-scope access; each 8-byte element is
-// still a single-copy-atomic relaxed access, which is all the tags need.
+// A published block sum is two 64-bit words, each holding one 32-bit half
+// of the value (low bits) under its bitwise complement (high bits).  Slots
+// start zeroed every launch, and (0, 0) fails the check, so a reader that
+// sees both words check has the whole value: no fence orders the halves.
+// The check also holds for any mix of a word's zeroed and written 32-bit
+// halves: (~h, 0) passes only when h == 0 and (0, h) only when
+// h == 0xffffffff, and in both cases that is exactly the written word.  So
+// copies that promise no single-copy atomicity above 32 bits (the default
+// form's bulk copies) still see each word as either written or not yet.
 __device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a, unsigned long long b)
 {
     asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
@@ -288,14 +292,21 @@ __device__ __forceinline__ void publish_block(unsigned long long *slot, C v)
     static_assert(sizeof(C) == 8, "64-bit carries");
     unsigned long long bits;
     memcpy(&bits, &v, 8);
-    st_relaxed_v2(slot, (1ull << 32) | (bits & 0xffffffffull), (1ull << 32) | (bits >> 32));
+    const unsigned long long lo = bits & 0xffffffffull, hi = bits >> 32;
+    st_relaxed_v2(slot, ((lo ^ 0xffffffffull) << 32) | lo, ((hi ^ 0xffffffffull) << 32) | hi);
 }
 
-// Decodes the two words of a slot; false while either tag is still zero.
+// A word is published when its high half is the complement of its low half.
+__device__ __forceinline__ bool word_published(unsigned long long w)
+{
+    return uint32_t(w >> 32) == ~uint32_t(w);
+}
+
+// Decodes the two words of a slot; false while either is not yet published.
 template <typename C>
 __device__ __forceinline__ bool decode_block(unsigned long long a, unsigned long long b, C &v)
 {
-    if ((a >> 32) == 0ull || (b >> 32) == 0ull)
+    if (!word_published(a) || !word_published(b))
         return false;
     const unsigned long long bits = (a & 0xffffffffull) | (b << 32);
     memcpy(&v, &bits, 8);
