@@ -46,7 +46,10 @@ T_BYTES = 2 * ROWS * COLS * ESIZE   # transpose: read + write
 R_BYTES = N_SUM * ESIZE             # sum: read
 STEP_BYTES = T_BYTES + R_BYTES
 WORKLOAD = "transpose 16384x16384 fp32 + sum 2^28 fp32, N(0,1), seed 1"
-METRIC = "transpose/reduce HBM GB/s (% of GB300 peak)"
+# The headline metric; `value` is its first clause (step GB/s), and the
+# batched and served req/s and p99 comparisons are the line's "batched" and
+# "served" objects.
+METRIC = "transpose/reduce HBM GB/s (% of GB300 peak); batched+served req/s and p99 vs plain"
 
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
