@@ -560,7 +560,6 @@ scan_onepass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_con
     using T = ScanTraits<DT>;
     using Acc = typename T::Acc;
     using Carry = typename T::Carry;
-    using Out = typename T::Out;
     constexpr int kWords = P::kWords;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[2];
@@ -763,7 +762,6 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
     using T = ScanTraits<DT>;
     using Acc = typename T::Acc;
     using Carry = typename T::Carry;
-    using Out = typename T::Out;
     constexpr int kWords = P::kWords;
     constexpr int kPubWarp = kScanThreads / 32 - 1;
     static_assert(kMaxLevels <= kPubWarp, "one warp per carry level, one to publish");
