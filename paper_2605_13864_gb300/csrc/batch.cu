@@ -378,7 +378,8 @@ optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t
     const size_t clear = clear_done > 0 ? size_t(reinterpret_cast<char *>(d_done + clear_done) -
                                                  reinterpret_cast<char *>(d_queue))
                                         : sizeof(unsigned long long);
-    if ((st = check_cuda(cudaMemsetAsync(d_queue, 0, clear, stream), "batch: reset queue")) != OPTIGPU_OK)
+    if (clear_done >= 0 &&
+        (st = check_cuda(cudaMemsetAsync(d_queue, 0, clear, stream), "batch: reset queue")) != OPTIGPU_OK)
         return st;
     int comp = compensated;
     void *args[] = {&d_insts, &d_item_inst, &items, &d_queue, &d_done, &d_partials, &comp};
@@ -757,50 +758,50 @@ optigpu_status seg_stage_buffer(cudaStream_t s, size_t bytes, void **buf, cudaEv
     return OPTIGPU_OK;
 }
 
-// Instance table of a segmented sum, one thread per segment: segment s is
-// instance s, its items (16384-element chunks) start at first[s], and an
-// empty segment gets no item and a zero result.
-__global__ void seg_instances_kernel(const char *src, int64_t esize, int dtype, char *out, const int64_t *offsets,
-                                     const int64_t *first, int32_t nseg, BatchInst *insts)
+// The tables of a segmented sum in one launch, one thread per segment and
+// per item.  Thread k < nseg writes instance k (segment k; its items, the
+// 16384-element chunks, start at first[k]; an empty segment gets no item and
+// a zero result) and zeroes its completion counter; thread i < items finds
+// its segment, the largest s with first[s] <= i, by binary search over
+// first[]; thread 0 also zeroes the work queue.
+__global__ void seg_tables_kernel(const char *src, int64_t esize, int dtype, char *out, const int64_t *offsets,
+                                  const int64_t *first, int32_t nseg, int64_t items, BatchInst *insts,
+                                  uint32_t *item_inst, unsigned long long *queue, unsigned *done)
 {
-    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k >= nseg)
-        return;
-    const int64_t len = offsets[k + 1] - offsets[k];
-    BatchInst b;
-    b.src = src + offsets[k] * esize;
-    b.dst = out + 8 * k;
-    b.rows = len;
-    b.cols = 1;
-    b.first_item = first[k];
-    b.aux = first[k]; // one partial per chunk, in item order
-    b.op = OPTIGPU_OP_REDUCE;
-    b.dtype = dtype;
-    b.nitems = int32_t((len + kReduceChunk - 1) / kReduceChunk);
-    b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
-    b.th_log2 = 0;
-    b.tw_log2 = 0;
-    insts[k] = b;
-    if (len == 0)
-        *reinterpret_cast<long long *>(out + 8 * k) = 0; // the same bits as int64 0 and double +0.0
-}
-
-// Item -> instance map, one thread per item: the segment whose items
-// [first[s], first[s + 1]) contain it (binary search over first[]).
-__global__ void seg_items_kernel(const int64_t *first, int32_t nseg, int64_t items, uint32_t *item_inst)
-{
-    const int64_t it = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (it >= items)
-        return;
-    int32_t lo = 0, hi = nseg - 1; // largest s with first[s] <= it and a non-empty range
-    while (lo < hi) {
-        const int32_t mid = lo + (hi - lo + 1) / 2;
-        if (first[mid] <= it)
-            lo = mid;
-        else
-            hi = mid - 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i == 0)
+        *queue = 0ull;
+    if (i < nseg) {
+        const int64_t len = offsets[i + 1] - offsets[i];
+        BatchInst b;
+        b.src = src + offsets[i] * esize;
+        b.dst = out + 8 * i;
+        b.rows = len;
+        b.cols = 1;
+        b.first_item = first[i];
+        b.aux = first[i]; // one partial per chunk, in item order
+        b.op = OPTIGPU_OP_REDUCE;
+        b.dtype = dtype;
+        b.nitems = int32_t((len + kReduceChunk - 1) / kReduceChunk);
+        b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
+        b.th_log2 = 0;
+        b.tw_log2 = 0;
+        insts[i] = b;
+        done[i] = 0u;
+        if (len == 0)
+            *reinterpret_cast<long long *>(out + 8 * i) = 0; // the same bits as int64 0 and double +0.0
     }
-    item_inst[it] = uint32_t(lo);
+    if (i < items) {
+        int32_t lo = 0, hi = nseg - 1; // largest s with first[s] <= i and a non-empty range
+        while (lo < hi) {
+            const int32_t mid = lo + (hi - lo + 1) / 2;
+            if (first[mid] <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        item_inst[i] = uint32_t(lo);
+    }
 }
 
 } // namespace
@@ -838,7 +839,7 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int config = 0;
     // Workspace: the batch tables (instance s = segment s), then the offsets
-    // and every segment's first item, which the two table kernels expand.
+    // and every segment's first item, which the table kernel expands.
     const BatchLayout L = batch_layout(nseg, std::max<int64_t>(items, 1), std::max<int64_t>(items, 1));
     const size_t meta_bytes = 2 * 8 * (size_t(nseg) + 1);
     const size_t off_meta = (L.total + 255) / 256 * 256;
@@ -869,15 +870,15 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
         return st;
     BatchInst *d_insts = reinterpret_cast<BatchInst *>(base + L.off_inst);
     uint32_t *d_items = reinterpret_cast<uint32_t *>(base + L.off_items);
-    seg_instances_kernel<<<unsigned((nseg + 255) / 256), 256, 0, s>>>(
+    auto *d_queue = reinterpret_cast<unsigned long long *>(base + L.off_queue);
+    auto *d_done = reinterpret_cast<unsigned *>(base + L.off_done);
+    const int64_t threads = std::max<int64_t>(nseg, items);
+    seg_tables_kernel<<<unsigned((threads + 255) / 256), 256, 0, s>>>(
         static_cast<const char *>(src), int64_t(es), int(dtype), static_cast<char *>(out), d_off, d_first, nseg,
-        d_insts);
-    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: instance table")) != OPTIGPU_OK || items == 0)
+        items, d_insts, d_items, d_queue, d_done);
+    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: tables")) != OPTIGPU_OK || items == 0)
         return st;
-    seg_items_kernel<<<unsigned((items + 255) / 256), 256, 0, s>>>(d_first, nseg, items, d_items);
-    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: item map")) != OPTIGPU_OK)
-        return st;
-    return batch_launch(config, d_insts, d_items, items, reinterpret_cast<unsigned long long *>(base + L.off_queue),
-                        reinterpret_cast<unsigned *>(base + L.off_done), nseg, base + L.off_part,
+    // The table kernel zeroed the queue and the counters (clear_done < 0).
+    return batch_launch(config, d_insts, d_items, items, d_queue, d_done, -1, base + L.off_part,
                         (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr);
 }

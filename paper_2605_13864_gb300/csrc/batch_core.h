@@ -66,7 +66,9 @@ int batch_tile(int config);
 // `clear_done` instances' completion counters are zeroed too (with the queue,
 // which the layout places right before them): callers whose workspace held
 // other tables before pass their instance count; plans, whose counters start
-// at zero and are left at zero by every run, pass 0.
+// at zero and are left at zero by every run, pass 0.  A negative `clear_done`
+// means the caller has already zeroed the queue and the counters in work
+// ordered before this launch on `stream`, so nothing is reset here.
 optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
                             unsigned long long *d_queue, unsigned *d_done, int64_t clear_done, void *d_partials,
                             int compensated, cudaStream_t stream, int *grid_out);
