@@ -64,9 +64,18 @@ constexpr int64_t kPiece = 32768; // bytes per work piece
 
 // Copies every piece of `count` descriptors; CTAs stride over pieces.  Each
 // piece uses the widest unit (16, 4 or 1 bytes) that both addresses allow.
+// CTA 0 also zeroes the step's batch queue and its first `ndone` completion
+// counters when `queue` is given (the batch kernel runs after this one).
 __global__ void __launch_bounds__(256) copy_pieces_kernel(const CopyDesc *__restrict__ d, int32_t count,
-                                                          int64_t pieces)
+                                                          int64_t pieces, unsigned long long *queue,
+                                                          unsigned *done, int32_t ndone)
 {
+    if (queue && blockIdx.x == 0) {
+        if (threadIdx.x == 0)
+            *queue = 0ull;
+        for (int32_t i = threadIdx.x; i < ndone; i += blockDim.x)
+            done[i] = 0u;
+    }
     for (int64_t p = blockIdx.x; p < pieces; p += gridDim.x) {
         int lo = 0, hi = count - 1;
         while (lo < hi) {
@@ -352,51 +361,59 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
             }
         }
         const int32_t n_scatter = int32_t(copies.size()) - n_gather;
+        // Workspace: the batch layout's queue, counters and tables, then the
+        // step's copy list right after the tables (so that tables and list
+        // go up in one copy), then the partials.
         const BatchLayout L = batch_layout(int64_t(descs.size()), t.items, t.chunks);
         const size_t table_bytes = L.off_part - L.off_inst;
-        const size_t off_copy = (L.total + 255) / 256 * 256;
         const size_t copy_bytes = sizeof(CopyDesc) * copies.size();
-        if ((st = ensure_capacity(sc, off_copy + copy_bytes, table_bytes + copy_bytes)) != OPTIGPU_OK)
+        const size_t off_copy = L.off_part;
+        const size_t off_part = round_up(off_copy + copy_bytes);
+        if ((st = ensure_capacity(sc, off_part + (L.total - L.off_part), table_bytes + copy_bytes)) != OPTIGPU_OK)
             return st;
         char *stage = static_cast<char *>(sc.h_stage);
         char *ws = static_cast<char *>(sc.d_ws);
         if (t.items > 0) {
             std::memcpy(stage, t.insts.data(), sizeof(BatchInst) * t.insts.size());
             std::memcpy(stage + (L.off_items - L.off_inst), t.item_inst.data(), sizeof(uint32_t) * t.item_inst.size());
-            if ((st = check_cuda(cudaMemcpyAsync(ws + L.off_inst, stage, table_bytes, cudaMemcpyHostToDevice, sc.s),
-                                 "server: copy step tables")) != OPTIGPU_OK)
-                return st;
         }
-        if (!copies.empty()) {
+        if (!copies.empty())
             std::memcpy(stage + table_bytes, copies.data(), copy_bytes);
-            if ((st = check_cuda(cudaMemcpyAsync(ws + off_copy, stage + table_bytes, copy_bytes,
-                                                 cudaMemcpyHostToDevice, sc.s),
-                                 "server: copy step copy list")) != OPTIGPU_OK)
-                return st;
-        }
+        if ((t.items > 0 || !copies.empty()) &&
+            (st = check_cuda(cudaMemcpyAsync(ws + L.off_inst, stage, table_bytes + copy_bytes, cudaMemcpyHostToDevice,
+                                             sc.s),
+                             "server: copy step tables and copy list")) != OPTIGPU_OK)
+            return st;
+        auto *d_queue = reinterpret_cast<unsigned long long *>(ws + L.off_queue);
+        auto *d_done = reinterpret_cast<unsigned *>(ws + L.off_done);
         DeviceInfo dev;
         if ((st = current_device(dev)) != OPTIGPU_OK)
             return st;
         const CopyDesc *d_copies = reinterpret_cast<const CopyDesc *>(ws + off_copy);
+        // The gather kernel, when there is one, also zeroes the batch queue
+        // and counters, and the batch launch then skips its reset memset.
+        const bool gather_clears = n_gather > 0 && t.items > 0;
         if (n_gather > 0) {
             const int64_t grid = std::min<int64_t>(gpieces, int64_t(4) * dev.num_sms);
-            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies, n_gather, gpieces);
+            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies, n_gather, gpieces,
+                                                                 gather_clears ? d_queue : nullptr, d_done,
+                                                                 int32_t(descs.size()));
             if ((st = check_cuda(cudaGetLastError(), "server: gather")) != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
         }
         if (t.items > 0) {
             if ((st = batch_launch(config, reinterpret_cast<BatchInst *>(ws + L.off_inst),
-                                   reinterpret_cast<uint32_t *>(ws + L.off_items), t.items,
-                                   reinterpret_cast<unsigned long long *>(ws + L.off_queue),
-                                   reinterpret_cast<unsigned *>(ws + L.off_done), int64_t(descs.size()),
-                                   ws + L.off_part, rflags ? 1 : 0, sc.s, nullptr)) != OPTIGPU_OK)
+                                   reinterpret_cast<uint32_t *>(ws + L.off_items), t.items, d_queue, d_done,
+                                   gather_clears ? -1 : int64_t(descs.size()), ws + off_part, rflags ? 1 : 0,
+                                   sc.s, nullptr)) != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
         }
         if (n_scatter > 0) {
             const int64_t grid = std::min<int64_t>(spieces, int64_t(4) * dev.num_sms);
-            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies + n_gather, n_scatter, spieces);
+            copy_pieces_kernel<<<unsigned(grid), 256, 0, sc.s>>>(d_copies + n_gather, n_scatter, spieces, nullptr,
+                                                                 nullptr, 0);
             if ((st = check_cuda(cudaGetLastError(), "server: scatter")) != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
