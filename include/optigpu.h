@@ -183,7 +183,9 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
  *   offsets  HOST array of nseg + 1 non-decreasing element offsets (< 2^40).
  *   out      device array of nseg 8-byte results (int64 / double); empty
  *            segments give 0.
- * All segments run in one launch of the batch kernel (one work item per
+ * The offsets go to the device in one asynchronous copy through pinned
+ * staging; one small kernel builds the batch tables from them, then all
+ * segments run in one launch of the batch kernel (one work item per
  * 16384-element chunk of every segment).  Uses a per-stream library
  * workspace (allocated on first use).  Errors as optigpu_reduce_sum_ex. */
 optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets, int32_t nseg,
