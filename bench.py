@@ -261,16 +261,32 @@ def measure_batched(steps: int = 10):
     return res
 
 
+def _host_reference(a, dtype: str):
+    """CPU references for the bench's own result checks (parity proper is in
+    tests/, against the oracle): int32 sums exact in int64, float sums in
+    float64 by numpy (pairwise: within about 1e-15 * sum|x|, and exact for
+    the precision vectors, whose values and partial sums are all exact in
+    float64), with sum|x| for the relative bound.  `a` holds bf16 as uint16
+    bits and fp16 as float16."""
+    if dtype == "int32":
+        return {"int": int(np.asarray(a, dtype=np.int64).sum())}
+    if dtype == "bfloat16":
+        x = (np.asarray(a).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    else:
+        x = np.asarray(a).astype(np.float64)
+    x = x.reshape(-1)
+    return {"f64": float(x.sum()), "abs": float(np.abs(x).sum())}
+
+
 def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: int = 400):
     """The serving workload: an open-loop Poisson stream of `count` requests
     at `rate` req/s (seed 4; op 50/50, dtype uniform over int32/fp32/bf16,
     sizes as in the batched workload) served under a 40 GB device budget by
     the continuous-batching server and by the per-call baseline; then both at
     saturation (every request queued at t = 0).  Inputs come from pinned host
-    payload pools (one per dtype); every sum and a sample of transposes are
-    checked against the CPU oracle."""
+    payload pools (one per dtype); a sample of sums and transposes is checked
+    against CPU references (numpy transposes, float64 sums)."""
     import torch
-    import oracle
     from paper_2605_13864_gb300 import api, workloads
 
     reqs = workloads.serving_requests(count=count, rate=rate, seed=4)
@@ -343,30 +359,39 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
         a = src.numpy() if dt != "bfloat16" else src.view(torch.int16).numpy().view(np.uint16)
         if op == "transpose":
             got = dst.numpy() if dt != "bfloat16" else dst.view(torch.int16).numpy().view(np.uint16)
-            good = np.array_equal(got.view(np.uint8), oracle.transpose(a).view(np.uint8))
+            good = np.array_equal(got.view(np.uint8), np.ascontiguousarray(a.T).view(np.uint8))
         elif dt == "int32":
-            good = int(dst.view(torch.int64).item()) == oracle.sum_i64(a)
+            good = int(dst.view(torch.int64).item()) == _host_reference(a, dt)["int"]
         else:
-            ref = oracle.reduce_reference(a, dt)
+            ref = _host_reference(a, dt)
             good = abs(float(dst.item()) - ref["f64"]) <= 1e-6 * ref["abs"] + 1e-300
         ok += int(good)
         bad += int(not good)
     res["checked"] = {"requests": ok + bad, "exact_or_within_tol": ok, "failed": bad,
-                      "what": f"{check_sample} sampled requests (sums and transposes) against the CPU oracle"}
+                      "what": f"{check_sample} sampled requests (sums and transposes) against CPU "
+                              "references (numpy transpose, float64 sums)"}
     # Offered-load sweep: the highest rate each mode sustains with p99 <= 1 ms.
+    # Near a mode's saturation p99 swings from run to run, so every rate runs
+    # three times (different arrival draws) and the point reports the medians.
     sweep_n = min(count, 20_000)
     for mode, (per_call, streams, slots) in shapes.items():
         sv = api.Server(budget_bytes=40 << 30, max_slots=slots, n_streams=streams, per_call=per_call)
         sv.replay(host[:1000], np.zeros(1000))
         points = []
         for rate_k in (20, 50, 100, 120, 150, 200, 225, 250, 275, 300, 400):
-            arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / (rate_k * 1e3), sweep_n))
-            t0 = time.perf_counter()
-            lat = sv.replay(host[:sweep_n], arr)
-            wall = time.perf_counter() - t0
-            points.append({"offered_req_per_s": rate_k * 1000, "achieved_req_per_s": round(sweep_n / wall, 1),
-                           "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 4),
-                           "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 4)})
+            runs = []
+            for rep in range(3):
+                arr = np.cumsum(np.random.default_rng(7 + rep).exponential(1.0 / (rate_k * 1e3), sweep_n))
+                t0 = time.perf_counter()
+                lat = sv.replay(host[:sweep_n], arr)
+                wall = time.perf_counter() - t0
+                runs.append((sweep_n / wall, float(np.percentile(lat, 50)) * 1e3,
+                             float(np.percentile(lat, 99)) * 1e3))
+            points.append({"offered_req_per_s": rate_k * 1000,
+                           "achieved_req_per_s": round(float(np.median([r[0] for r in runs])), 1),
+                           "p50_ms": round(float(np.median([r[1] for r in runs])), 4),
+                           "p99_ms": round(float(np.median([r[2] for r in runs])), 4),
+                           "p99_ms_runs": [round(r[2], 4) for r in runs]})
         sv.close()
         ok = [p for p in points if p["p99_ms"] <= 1.0]
         res[mode]["load_sweep"] = points
@@ -382,16 +407,18 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
 def measure_precision():
     """The precision workload: 2^28 N(100,1) values rounded to bf16 and to
     fp16 (seed 2), summed in FP32 plain and compensated with the FP64 final
-    combine; errors against the exact FP64 oracle.  Plus the 8192x8192 bf16
-    transpose, checked bit-exact."""
+    combine; errors against the exact sum (the values are multiples of 2^-4
+    and every partial sum is below 2^35, so a float64 sum in any order is
+    exact).  Plus the 8192x8192 bf16 transpose, checked bit-exact against
+    numpy."""
     import torch
-    import oracle
     from paper_2605_13864_gb300 import api, workloads
 
     vb, vh = workloads.precision_vectors()
     res = {"workload": "2^28 N(100,1) rounded to bf16 / fp16 (seed 2); bf16 8192x8192 N(0,1) transpose"}
     for name, v, tdt in (("bf16", vb, torch.bfloat16), ("fp16", vh, torch.float16)):
-        ref = oracle.reduce_reference(v, "bfloat16" if name == "bf16" else "float16")
+        ref = _host_reference(v.view(np.uint16) if name == "bf16" else v.view(np.float16),
+                              "bfloat16" if name == "bf16" else "float16")
         d = torch.from_numpy(v.view(np.int16)).view(tdt).cuda()
         out = torch.empty((), dtype=torch.float64, device="cuda")
         for comp in (False, True):
@@ -407,7 +434,7 @@ def measure_precision():
             got = out.item()
             err = abs(got - ref["f64"])
             res[f"{name}_{'compensated' if comp else 'plain'}"] = {
-                "sum": got, "oracle_fp64": ref["f64"], "abs_error": err,
+                "sum": got, "exact_fp64": ref["f64"], "abs_error": err,
                 "rel_error_vs_sum_abs": err / ref["abs"], "within_1e-6": err <= 1e-6 * ref["abs"],
                 "ms": round(ms, 4), "gbs": round(v.nbytes / ms / 1e6, 1)}
         del d
@@ -422,7 +449,8 @@ def measure_precision():
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 20
-    exact = np.array_equal(o.view(torch.int16).cpu().numpy().view(np.uint16), oracle.transpose(m))
+    exact = np.array_equal(o.view(torch.int16).cpu().numpy().view(np.uint16),
+                           np.ascontiguousarray(m.view(np.uint16).T))
     res["bf16_transpose_8192"] = {"bit_exact": bool(exact), "ms": round(ms, 4),
                                   "gbs": round(2 * m.nbytes / ms / 1e6, 1)}
     del d, o
