@@ -283,7 +283,8 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
     at `rate` req/s (seed 4; op 50/50, dtype uniform over int32/fp32/bf16,
     sizes as in the batched workload) served under a 40 GB device budget by
     the continuous-batching server and by the per-call baseline; then both at
-    saturation (every request queued at t = 0).  Inputs come from pinned host
+    saturation (every request queued at t = 0).  Each is run three times and
+    reported as medians.  Inputs come from pinned host
     payload pools (one per dtype); a sample of sums and transposes is checked
     against CPU references (numpy transposes, float64 sums)."""
     import torch
@@ -336,18 +337,28 @@ def measure_served(count: int = 100_000, rate: float = 20_000.0, check_sample: i
     for mode, (per_call, streams, slots) in shapes.items():
         sv = api.Server(budget_bytes=40 << 30, max_slots=slots, n_streams=streams, per_call=per_call)
         sv.replay(host[:2000], arrivals[:2000] * 0)  # warm-up: kernels loaded, workspaces sized
-        t0 = time.perf_counter()
-        lat = sv.replay(host, arrivals)
-        wall = time.perf_counter() - t0
-        st = sv.stats()
-        t1 = time.perf_counter()
+        # The trace runs three times and each figure is the median: on a
+        # shared host one run now and then meets a stall of ~0.1 s, which
+        # alone moves its p99 by orders of magnitude.
+        runs, st = [], None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            lat = sv.replay(host, arrivals)
+            wall = time.perf_counter() - t0
+            if st is None:
+                st = sv.stats()
+            runs.append((count / wall, float(np.percentile(lat, 50)) * 1e3, float(np.percentile(lat, 99)) * 1e3,
+                         float(lat.mean()) * 1e3))
         sat_n = min(count, 20_000)
-        sv.replay(host[:sat_n], np.zeros(sat_n))
-        sat = time.perf_counter() - t1
-        res[mode] = {"req_per_s": round(count / wall, 1), "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 4),
-                     "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 4),
-                     "mean_ms": round(float(lat.mean()) * 1e3, 4),
-                     "saturated_req_per_s": round(sat_n / sat, 1),
+        sats = []
+        for _ in range(3):
+            t1 = time.perf_counter()
+            sv.replay(host[:sat_n], np.zeros(sat_n))
+            sats.append(sat_n / (time.perf_counter() - t1))
+        med = lambda i: float(np.median([r[i] for r in runs]))
+        res[mode] = {"req_per_s": round(med(0), 1), "p50_ms": round(med(1), 4), "p99_ms": round(med(2), 4),
+                     "mean_ms": round(med(3), 4), "p99_ms_runs": [round(r[2], 4) for r in runs],
+                     "saturated_req_per_s": round(float(np.median(sats)), 1),
                      "steps": st["steps"], "kernel_launches": st["launches"],
                      "max_in_flight": st["max_in_flight"], "peak_device_bytes": st["peak_bytes"],
                      "streams": streams, "max_slots": slots}
