@@ -76,3 +76,25 @@ def test_reference_arm_rank0_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["metric"] == bench.METRIC
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_host_reference_agrees_with_the_oracle():
+    # The bench's own result checks (served sample, precision errors) use
+    # numpy references; here they are held to the oracle on small inputs.
+    import numpy as np
+
+    import oracle
+    from paper_2605_13864_gb300 import workloads
+
+    vb, vh = workloads.precision_vectors(1 << 16)
+    rb = bench._host_reference(vb.view(np.uint16), "bfloat16")
+    rh = bench._host_reference(vh.view(np.float16), "float16")
+    assert rb["f64"] == oracle.reduce_reference(vb, "bfloat16")["f64"]   # exact sums
+    assert rh["f64"] == oracle.reduce_reference(vh, "float16")["f64"]
+    x = workloads.vector(100003, "float32", seed=9)
+    r, o = bench._host_reference(x, "float32"), oracle.reduce_reference(x)
+    assert abs(r["f64"] - o["f64"]) <= 1e-12 * o["abs"] and abs(r["abs"] - o["abs"]) <= 1e-12 * o["abs"]
+    xi = workloads.vector(100003, "int32", seed=9)
+    assert bench._host_reference(xi, "int32")["int"] == oracle.sum_i64(xi)
+    m = workloads.matrix(37, 53, "float32", seed=9)
+    assert np.array_equal(np.ascontiguousarray(m.T), oracle.transpose(m))
