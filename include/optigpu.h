@@ -165,8 +165,10 @@ int optigpu_transpose_tma_eligible(const void *src, const void *dst,
  *         the GPU (no float atomics); the FP32 value is (float)*out.
  *   n     >= 0 and < 2^62.  n == 0 writes 0.
  * Uses a per-stream library workspace of 8 * ceil(n / CHUNK) + 256 bytes,
- * allocated with cudaMalloc on first use (and grown on demand), so the first
- * call on a stream must not happen during stream capture.
+ * allocated with cudaMalloc on first use, so the first call on a stream must
+ * not happen during stream capture.  A later, larger sum on the stream gets a
+ * new, larger workspace; the old one is retired but stays allocated until
+ * optigpu_release_workspaces(), so a CUDA graph captured with it stays valid.
  * Returns INVALID_ARG, UNSUPPORTED_DTYPE, OOM or CUDA. */
 optigpu_status optigpu_reduce_sum(const void *src, int64_t n,
                                   optigpu_dtype dtype, void *out,
@@ -227,8 +229,9 @@ optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, int64_t lo, 
 
 /* Allocates (or grows) the workspace `stream` needs for sums of up to n
  * elements, so that later sums on that stream -- for example inside a CUDA
- * graph capture -- allocate nothing.  INVALID_ARG for n < 0, OOM on
- * allocation failure. */
+ * graph capture -- allocate nothing.  Growing never frees a workspace that a
+ * captured graph may still use (see optigpu_release_workspaces).
+ * INVALID_ARG for n < 0, OOM on allocation failure. */
 optigpu_status optigpu_reduce_reserve(int64_t n, optigpu_stream_t stream);
 
 /* Allocation-free sum.  The thesis has no counterpart to this entry point:
@@ -246,7 +249,9 @@ optigpu_status optigpu_reduce_reserve(int64_t n, optigpu_stream_t stream);
  *   returns INVALID_ARG with that limit in optigpu_last_error().
  *   The first call on a device looks up the array's device address (set-up,
  *   once per device, with that device current); make that first call before
- *   any stream capture.
+ *   any stream capture.  cudaDeviceReset() invalidates that address: after a
+ *   reset, call optigpu_release_workspaces() (which forgets it) before the
+ *   next call on that device.
  *   All calls share the one array: calls whose kernels overlap on the GPU
  *   (for example on two streams at once) race and give wrong sums.  Order
  *   them, e.g. by issuing them on one stream. */
@@ -374,17 +379,30 @@ typedef struct {
 typedef struct {
     int64_t submitted, completed, pending, in_flight, max_in_flight;
     int64_t steps;    /* launched steps (stream submissions) */
-    int64_t launches; /* kernel launches (1 per batched step; 1 per request in per-call mode) */
+    int64_t launches; /* kernel launches, copy kernels included (per batched step: gather, batch
+                         kernel, scatter; per request in per-call mode: the plain kernel, plus a
+                         gather and a scatter with OPTIGPU_SERVER_COPY_KERNELS) */
     int64_t bytes_in_use, peak_bytes; /* device arena */
+    int64_t replay_max_loop_gap_ns;   /* last optigpu_server_replay: longest time between two
+                                         rounds of its serving loop (a host-side stall) */
 } optigpu_server_stats;
 
 /* Server flags (OPTIGPU_REDUCE_COMPENSATED applies to every float sum). */
 #define OPTIGPU_SERVER_PER_CALL 4u /* baseline: one plain kernel per request, one request per stream */
+/* Copy path, held fixed to compare the modes.  By default a batched step
+ * moves pinned request buffers with two SM copy kernels (a gather and a
+ * scatter through the device's mapping of the host memory) and per-call mode
+ * uses one copy-engine call (cudaMemcpyAsync) per buffer; pageable buffers
+ * always go through the copy engines. */
+#define OPTIGPU_SERVER_COPY_ENGINES 8u  /* every buffer by a copy-engine call, batched mode too */
+#define OPTIGPU_SERVER_COPY_KERNELS 16u /* per-call mode: pinned buffers by one gather and one
+                                           scatter copy kernel per request */
 
 /* Creates a server with a device arena of mem_budget_bytes (one cudaMalloc,
  * >= 1 MiB), at most max_slots requests on the device at once and n_streams
  * streams (1..1024; at most n_streams steps in flight).  INVALID_ARG for bad
- * sizes or flags, OOM if the budget cannot be allocated. */
+ * sizes or flags (COPY_ENGINES with COPY_KERNELS), OOM if the budget cannot
+ * be allocated. */
 optigpu_status optigpu_server_create(size_t mem_budget_bytes, int32_t max_slots,
                                      int32_t n_streams, uint32_t flags,
                                      optigpu_server **server);
@@ -398,7 +416,10 @@ optigpu_status optigpu_server_submit(optigpu_server *server, const optigpu_reque
 /* One round of the loop: completes finished steps, admits queued requests in
  * arrival order into every free stream while slots and budget allow (one
  * step takes at most max_slots / n_streams requests, so steps overlap), and
- * launches them.  *launched (may be NULL) = number of steps launched. */
+ * launches them.  *launched (may be NULL) = number of steps launched.
+ * If a step's launch fails, the call waits for that step's stream, returns
+ * the step's requests to the head of the queue (their arena space and slots
+ * are freed) and returns the error (CUDA or OOM); a later step retries them. */
 optigpu_status optigpu_server_step(optigpu_server *server, int32_t *launched);
 
 /* *done = 1 once the ticket's result is in its host buffer (the ticket is
@@ -416,6 +437,14 @@ optigpu_status optigpu_server_get_stats(optigpu_server *server, optigpu_server_s
  * (the host sees the step's event fire) - arrival time. */
 optigpu_status optigpu_server_replay(optigpu_server *server, const optigpu_request *reqs,
                                      const double *arrival_s, int64_t count, double *latency_s);
+
+/* Testing hook (the thesis has no counterpart): the nth step launch from now
+ * on (1 = the next; 0 cancels) fails on the host part-way through (after any
+ * copy-engine input copies are enqueued), as a failed CUDA call would, so
+ * that the recovery described at optigpu_server_step can be exercised
+ * without a device fault.
+ * INVALID_ARG for a null server or nth < 0. */
+optigpu_status optigpu_server_inject_step_failure(optigpu_server *server, int32_t nth);
 
 /* Waits for the server's streams and frees everything it owns. */
 void optigpu_server_destroy(optigpu_server *server);
@@ -499,8 +528,11 @@ const char *optigpu_last_error(void);
  * (default 2e9, or the OPTIGPU_WAIT_LIMIT_NS environment variable). */
 void optigpu_set_wait_limit_ns(uint64_t ns);
 
-/* Frees every workspace the library holds for the current device (call with
- * no work in flight on the library's streams). */
+/* Frees every workspace the library holds for the current device, including
+ * those retired when a stream needed a larger one.  Call it with no work in
+ * flight on the library's streams, and only once no CUDA graph captured from
+ * the library's calls will be replayed again (such graphs keep the
+ * workspace addresses they were captured with). */
 optigpu_status optigpu_release_workspaces(void);
 
 /* OPTIGPU_VERSION of the loaded library. */

@@ -71,6 +71,7 @@ SIGNATURES = {
     "optigpu_server_drain": (_ci, [_vp]),
     "optigpu_server_get_stats": (_ci, [_vp, _vp]),
     "optigpu_server_replay": (_ci, [_vp, _vp, _vp, _i64, _vp]),
+    "optigpu_server_inject_step_failure": (_ci, [_vp, ctypes.c_int32]),
     "optigpu_server_destroy": (None, [_vp]),
     "optigpu_tune_num_configs": (_ci, [_ci, _ci]),
     "optigpu_tune_config_name": (ctypes.c_char_p, [_ci, _ci, _ci]),
@@ -107,10 +108,12 @@ class Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "pending", "in_flight",
                                                "max_in_flight", "steps", "launches", "bytes_in_use",
-                                               "peak_bytes")]
+                                               "peak_bytes", "replay_max_loop_gap_ns")]
 
 
 SERVER_PER_CALL = 4
+SERVER_COPY_ENGINES = 8
+SERVER_COPY_KERNELS = 16
 BATCH_NO_GRAPH = 2
 OP_BATCH = 2
 OP_SCAN = 3

@@ -343,13 +343,22 @@ class Server:
 
     Pinned host tensors (``tensor.pin_memory()``) make the copies
     asynchronous.  ``per_call=True`` is the baseline that launches one plain
-    kernel per request.
+    kernel per request.  ``copy`` picks the copy path of pinned buffers:
+    None (batched: SM copy kernels; per-call: copy engines), ``"engines"``
+    (copy-engine calls in both modes) or ``"kernels"`` (SM copy kernels in
+    both modes).
     """
 
     def __init__(self, budget_bytes: int = 1 << 30, max_slots: int = 256, n_streams: int = 4,
-                 per_call: bool = False, compensated: bool = False):
+                 per_call: bool = False, compensated: bool = False, copy: str | None = None):
         import ctypes
         flags = (N.SERVER_PER_CALL if per_call else 0) | (N.REDUCE_COMPENSATED if compensated else 0)
+        if copy == "engines" and not per_call:
+            flags |= N.SERVER_COPY_ENGINES
+        elif copy == "kernels" and per_call:
+            flags |= N.SERVER_COPY_KERNELS
+        elif copy not in (None, "engines", "kernels"):
+            raise ValueError("copy must be None, 'engines' or 'kernels'")
         h = ctypes.c_void_p()
         N.check(N.lib().optigpu_server_create(int(budget_bytes), int(max_slots), int(n_streams), flags,
                                               ctypes.byref(h)), "optigpu_server_create")
@@ -380,6 +389,11 @@ class Server:
 
     def drain(self) -> None:
         N.check(N.lib().optigpu_server_drain(self._h), "optigpu_server_drain")
+
+    def inject_step_failure(self, nth: int = 1) -> None:
+        """Testing hook: the nth step launch from now on fails on the host."""
+        N.check(N.lib().optigpu_server_inject_step_failure(self._h, int(nth)),
+                "optigpu_server_inject_step_failure")
 
     def stats(self) -> dict:
         import ctypes

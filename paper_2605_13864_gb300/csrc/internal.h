@@ -58,10 +58,12 @@ optigpu_status current_device(DeviceInfo &out);
 // Device-side wait limit handed to kernels that spin (ns).
 uint64_t wait_limit_ns();
 
-// A per-(device, stream) scratch buffer.  The returned pointer stays valid
-// until a later call on the same stream asks for more bytes (then it is
-// reallocated) or optigpu_release_workspaces() runs.  A new buffer is cleared
-// to zero (on `stream`), so counters kept in it start at 0.
+// A per-(device, stream) scratch buffer.  A later call on the same stream
+// that asks for more bytes gets a new, larger buffer; the old one is retired
+// (kept allocated), so kernels still queued and CUDA graphs captured with it
+// keep valid memory.  Every buffer, current or retired, stays allocated until
+// optigpu_release_workspaces() runs.  A new buffer is cleared to zero (on
+// `stream`), so counters kept in it start at 0.
 // `slot` separates workspaces with different layouts on one stream (0: the
 // single-call sum; 1: segmented sums).
 optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, int slot = 0);
@@ -111,6 +113,8 @@ optigpu_status reduce_band(const void *band_src, int64_t band_n, int dtype, uint
                            int64_t chunk_base, cudaStream_t stream);
 optigpu_status reduce_final(const void *partials, int64_t count, int dtype, uint32_t flags, void *out,
                             cudaStream_t stream);
+// Forgets the allocation-free sum's cached scratch address on `device`.
+void noalloc_forget_device(int device);
 optigpu_status transpose_dispatch(const void *src, void *dst, int64_t rows, int64_t cols, int dtype, int kernel,
                                   cudaStream_t stream);
 // Same with row pitches: dst[c * ldd + r] = src[r * lds + c].

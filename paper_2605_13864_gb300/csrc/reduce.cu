@@ -43,12 +43,20 @@
 namespace optigpu {
 namespace {
 
-template <int DT, bool COMP>
-__global__ void __launch_bounds__(kReduceThreads)
+// Two forms of one kernel, the same bits (ReduceCore's MAX_BATCH changes
+// only when loads are issued):
+//   WAVE = false  8 loads in flight per thread, at most 48 registers (5 CTAs
+//                 per SM): the throughput form for large sums;
+//   WAVE = true   4 loads in flight, at most 32 registers, so 8 CTAs fit on
+//                 an SM -- 1216 CTAs on 152 SMs, and a sum of up to that many
+//                 chunks (2^24 elements is 1024) starts all its chunks at
+//                 once instead of running a second, partial wave.
+template <int DT, bool COMP, bool WAVE>
+__global__ void __launch_bounds__(kReduceThreads, WAVE ? 8 : 5)
 reduce_sum_kernel(const void *__restrict__ src, int64_t n, int vec_ok, void *partials,
                   unsigned *counter, void *out, int64_t num_chunks)
 {
-    using Core = ReduceCore<DT, COMP>;
+    using Core = ReduceCore<DT, COMP, WAVE ? 4 : 8>;
     __shared__ typename Core::Shared sh;
     __shared__ int s_last;
     for (int64_t c = blockIdx.x; c < num_chunks; c += gridDim.x) {
@@ -56,12 +64,13 @@ reduce_sum_kernel(const void *__restrict__ src, int64_t n, int vec_ok, void *par
         if (threadIdx.x == 0)
             Core::store_partial(partials, c, part);
     }
-    // Completion: publish this CTA's partials, count it, and let the last CTA
-    // run the final combine.
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0)
+    // Completion: thread 0 wrote every partial of this CTA; it makes them
+    // visible GPU-wide, then counts the CTA; the last CTA runs the final
+    // combine.
+    if (threadIdx.x == 0) {
+        __threadfence();
         s_last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
     __syncthreads();
     if (!s_last)
         return;
@@ -110,45 +119,87 @@ struct KernelFacts {
     int ctas_per_sm = 0;
 };
 std::mutex g_mu;
-KernelFacts g_facts[64][4][2];
+KernelFacts g_facts[64][4][2][2];
 
+// Resident CTAs per SM of reduce_sum_kernel<DT, COMP, WAVE> (occupancy,
+// looked up once per device and kernel).
+template <int DT, bool COMP, bool WAVE>
+optigpu_status resident_ctas(const DeviceInfo &dev, int *ctas_per_sm)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    KernelFacts &f = g_facts[dev.device & 63][DT][COMP ? 1 : 0][WAVE ? 1 : 0];
+    if (!f.ready) {
+        const void *fn = reinterpret_cast<const void *>(&reduce_sum_kernel<DT, COMP, WAVE>);
+        int k = 0;
+        optigpu_status st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, kReduceThreads, 0),
+                                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(reduce)");
+        if (st != OPTIGPU_OK)
+            return st;
+        f.ctas_per_sm = std::max(k, 1);
+        f.ready = true;
+    }
+    *ctas_per_sm = f.ctas_per_sm;
+    return OPTIGPU_OK;
+}
+
+// Form and persistent grid of the sum for `num_chunks` chunks on the current
+// device.  The one-wave form is taken when all chunks fit in one wave of it;
+// otherwise the throughput form, with its resident CTAs per SM capped by the
+// tuned configuration.  Neither choice changes the result.
 template <int DT, bool COMP>
-optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream)
+optigpu_status persistent_grid(int64_t num_chunks, int64_t *grid, bool *wave)
 {
     DeviceInfo dev;
     optigpu_status st = current_device(dev);
     if (st != OPTIGPU_OK)
         return st;
-    const void *fn = reinterpret_cast<const void *>(&reduce_sum_kernel<DT, COMP>);
-    int ctas_per_sm = 1;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        KernelFacts &f = g_facts[dev.device & 63][DT][COMP ? 1 : 0];
-        if (!f.ready) {
-            int k = 0;
-            st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, kReduceThreads, 0),
-                            "cudaOccupancyMaxActiveBlocksPerMultiprocessor(reduce)");
-            if (st != OPTIGPU_OK)
-                return st;
-            f.ctas_per_sm = std::max(k, 1);
-            f.ready = true;
-        }
-        ctas_per_sm = f.ctas_per_sm;
+    int per_sm = 1;
+    if ((st = resident_ctas<DT, COMP, true>(dev, &per_sm)) != OPTIGPU_OK)
+        return st;
+    if (num_chunks <= int64_t(per_sm) * dev.num_sms) {
+        *wave = true;
+        *grid = num_chunks;
+        return OPTIGPU_OK;
     }
+    if ((st = resident_ctas<DT, COMP, false>(dev, &per_sm)) != OPTIGPU_OK)
+        return st;
     const int cap = kReduceCtasPerSm[g_reduce_choice.load()];
     if (cap > 0)
-        ctas_per_sm = std::min(ctas_per_sm, cap);
+        per_sm = std::min(per_sm, cap);
+    *wave = false;
+    *grid = std::min<int64_t>(num_chunks, int64_t(per_sm) * dev.num_sms);
+    return OPTIGPU_OK;
+}
+
+template <int DT, bool COMP>
+void launch_sum_kernel(bool wave, int64_t grid, cudaStream_t stream, const void *src, int64_t n, int vec_ok,
+                       void *partials, unsigned *counter, void *out, int64_t num_chunks)
+{
+    if (wave)
+        reduce_sum_kernel<DT, COMP, true><<<unsigned(grid), kReduceThreads, 0, stream>>>(
+            src, n, vec_ok, partials, counter, out, num_chunks);
+    else
+        reduce_sum_kernel<DT, COMP, false><<<unsigned(grid), kReduceThreads, 0, stream>>>(
+            src, n, vec_ok, partials, counter, out, num_chunks);
+}
+
+template <int DT, bool COMP>
+optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream)
+{
     const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
+    int64_t grid = 0;
+    bool wave = false;
+    optigpu_status st = persistent_grid<DT, COMP>(num_chunks, &grid, &wave);
+    if (st != OPTIGPU_OK)
+        return st;
     void *ws = nullptr;
     const size_t bytes = kReduceCounterBytes + size_t(num_chunks) * 8;
     if ((st = stream_workspace(stream, bytes, &ws)) != OPTIGPU_OK)
         return st;
     unsigned *counter = static_cast<unsigned *>(ws);
     void *partials = static_cast<char *>(ws) + kReduceCounterBytes;
-    const int64_t grid = std::min<int64_t>(num_chunks, int64_t(ctas_per_sm) * dev.num_sms);
     const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
-    reduce_sum_kernel<DT, COMP><<<unsigned(grid), kReduceThreads, 0, stream>>>(src, n, vec_ok, partials,
-                                                                             counter, out, num_chunks);
+    launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out, num_chunks);
     return check_cuda(cudaGetLastError(), "launch reduce");
 }
 
@@ -339,25 +390,36 @@ optigpu_status noalloc_scratch(void **addr)
     return OPTIGPU_OK;
 }
 
+} // namespace
+
+// Drops the looked-up address of the scratch array on `device` (after
+// cudaDeviceReset the module is loaded again and the array may move); the
+// next call on that device looks it up afresh.
+void noalloc_forget_device(int device)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    g_noalloc_addr.erase(device);
+}
+
+namespace {
+
 template <int DT, bool COMP>
 optigpu_status launch_noalloc(const void *src, int64_t n, void *out, cudaStream_t stream)
 {
-    DeviceInfo dev;
-    optigpu_status st = current_device(dev);
-    if (st != OPTIGPU_OK)
-        return st;
     const int64_t num_chunks = (n + kReduceChunk - 1) / kReduceChunk;
     if (num_chunks > kNoAllocMaxChunks)
         return fail(OPTIGPU_ERR_INVALID_ARG,
                     "reduce_sum_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
                         std::to_string(kNoAllocMaxChunks * kReduceChunk) + " elements");
     void *scratch = nullptr;
-    if ((st = noalloc_scratch(&scratch)) != OPTIGPU_OK)
+    optigpu_status st = noalloc_scratch(&scratch);
+    if (st != OPTIGPU_OK)
         return st;
-    const void *fn = reinterpret_cast<const void *>(&reduce_sum_kernel<DT, COMP>);
-    int ctas_per_sm = 0;
-    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, fn, kReduceThreads, 0),
-                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(reduce)")) != OPTIGPU_OK)
+    // The same kernel form and grid as optigpu_reduce_sum_ex (the result
+    // depends on neither; the occupancy is looked up once per device).
+    int64_t grid = 0;
+    bool wave = false;
+    if ((st = persistent_grid<DT, COMP>(num_chunks, &grid, &wave)) != OPTIGPU_OK)
         return st;
     unsigned *counter = static_cast<unsigned *>(scratch);
     void *partials = static_cast<char *>(scratch) + kReduceCounterBytes;
@@ -366,10 +428,8 @@ optigpu_status launch_noalloc(const void *src, int64_t n, void *out, cudaStream_
     if ((st = check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), stream),
                          "reduce_sum_noalloc: clear counter")) != OPTIGPU_OK)
         return st;
-    const int64_t grid = std::min<int64_t>(num_chunks, int64_t(std::max(ctas_per_sm, 1)) * dev.num_sms);
     const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
-    reduce_sum_kernel<DT, COMP><<<unsigned(grid), kReduceThreads, 0, stream>>>(src, n, vec_ok, partials, counter,
-                                                                             out, num_chunks);
+    launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out, num_chunks);
     return check_cuda(cudaGetLastError(), "launch reduce (noalloc)");
 }
 

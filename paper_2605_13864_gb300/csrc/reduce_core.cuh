@@ -186,13 +186,17 @@ struct Acc<DT, true> {
     }
 };
 
-template <int DT, bool COMP>
+// MAX_BATCH bounds the 16-byte loads a thread has in flight (8: the
+// throughput form; 4: fewer registers, so more CTAs fit on an SM).  It only
+// changes when loads are issued, never the order of the additions, so both
+// forms give the same bits.
+template <int DT, bool COMP, int MAX_BATCH = 8>
 struct ReduceCore {
     using T = ElemTraits<DT>;
     using A = Acc<DT, COMP>;
     static constexpr int V = T::V;
     static constexpr int VPT = int(kReduceChunk / V / kReduceThreads); // vectors per thread
-    static constexpr int BATCH = VPT < 8 ? VPT : 8;                     // loads in flight
+    static constexpr int BATCH = VPT < MAX_BATCH ? VPT : MAX_BATCH;     // loads in flight
     static_assert(VPT % BATCH == 0, "chunk must split into whole load batches");
     static constexpr bool kInt = (DT == OPTIGPU_INT32);
     using Partial = typename std::conditional<kInt, long long, double>::type;
@@ -284,13 +288,26 @@ struct ReduceCore {
 
     // Fixed-order combine of partials[0 .. count): thread t sums entries
     // t, t + 256, ... sequentially, then the same shuffle trees.  Thread 0
-    // writes the result to *out.
+    // writes the result to *out.  Each thread issues the loads of 4 entries
+    // before adding them (in the same order), so a combine of up to 1024
+    // partials costs one round trip to L2 instead of one per entry.
     __device__ static void final_combine(const void *partials, int64_t count, void *out, Shared &sh)
     {
+        constexpr int U = 4;
         const Partial *p = static_cast<const Partial *>(partials);
         Partial s = 0;
-        for (int64_t i = threadIdx.x; i < count; i += kReduceThreads)
-            s += __ldcg(p + i);
+        for (int64_t i0 = threadIdx.x; i0 < count; i0 += int64_t(U) * kReduceThreads) {
+            Partial v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + int64_t(u) * kReduceThreads;
+                v[u] = i < count ? __ldcg(p + i) : Partial(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + int64_t(u) * kReduceThreads < count)
+                    s += v[u];
+        }
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1)
             s += __shfl_xor_sync(0xffffffffu, s, m);

@@ -42,6 +42,10 @@ struct WsKey {
     }
 };
 std::map<WsKey, Workspace> g_workspaces;
+// Buffers replaced by larger ones.  A CUDA graph captured while one of them
+// was current keeps its address, so they stay allocated until
+// optigpu_release_workspaces() (device -> pointers).
+std::multimap<int, void *> g_retired;
 
 uint64_t g_wait_limit_ns = 0;
 
@@ -122,14 +126,6 @@ optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, i
     std::lock_guard<std::mutex> lk(g_mu);
     Workspace &ws = g_workspaces[WsKey{dev, stream, slot}];
     if (ws.bytes < bytes) {
-        if (ws.ptr) {
-            // The old buffer may still be in use by work queued on `stream`.
-            if ((st = check_cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize")) != OPTIGPU_OK)
-                return st;
-            cudaFree(ws.ptr);
-            ws.ptr = nullptr;
-            ws.bytes = 0;
-        }
         size_t want = bytes < (size_t(1) << 16) ? (size_t(1) << 16) : bytes + bytes / 2;
         void *p = nullptr;
         if ((st = check_cuda(cudaMalloc(&p, want), "cudaMalloc(workspace)")) != OPTIGPU_OK)
@@ -140,6 +136,10 @@ optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, i
             cudaFree(p);
             return st;
         }
+        // The old buffer is retired, not freed: work queued on `stream` and
+        // graphs captured from it may still use it.
+        if (ws.ptr)
+            g_retired.emplace(dev, ws.ptr);
         ws.ptr = p;
         ws.bytes = want;
     }
@@ -316,6 +316,14 @@ optigpu_status optigpu_release_workspaces(void)
             ++it;
         }
     }
+    auto range = g_retired.equal_range(dev);
+    for (auto it = range.first; it != range.second; ++it)
+        cudaFree(it->second);
+    g_retired.erase(range.first, range.second);
+    // Cached device addresses of module globals are looked up again on next
+    // use (they move if the device was reset).
+    g_devices.erase(dev);
+    noalloc_forget_device(dev);
     return OPTIGPU_OK;
 }
 

@@ -22,7 +22,17 @@
 //
 // With OPTIGPU_SERVER_PER_CALL the same loop launches one plain kernel per
 // request (optigpu_transpose / optigpu_reduce_sum_ex), one request per
-// stream: the per-call baseline.
+// stream: the per-call baseline.  Two flags hold the copy path fixed across
+// both modes, so that batching can be measured apart from it:
+// OPTIGPU_SERVER_COPY_ENGINES copies every buffer with a copy-engine call
+// (also in batched mode), OPTIGPU_SERVER_COPY_KERNELS moves pinned buffers
+// with SM copy kernels in per-call mode too (one gather and one scatter
+// launch per request).
+//
+// If launching a step fails, nothing of it stays on the device: its stream is
+// drained, its requests give back their arena space and slots and return to
+// the head of the queue in their order, and the error is returned; a later
+// step tries them again.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -110,6 +120,26 @@ __global__ void __launch_bounds__(256) copy_pieces_kernel(const CopyDesc *__rest
         for (int64_t i = done + threadIdx.x; i < len; i += blockDim.x)
             dst[i] = src[i];
     }
+}
+
+// Copies one contiguous range (a request's buffer in per-call mode with copy
+// kernels); CTAs stride over 16-byte units when both ends allow, else bytes.
+__global__ void __launch_bounds__(256) copy_range_kernel(const char *__restrict__ src, char *__restrict__ dst,
+                                                         int64_t bytes)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t first = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+        const int64_t n = bytes / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int64_t i = first; i < n; i += stride)
+            d4[i] = s4[i];
+        done = n * 16;
+    }
+    for (int64_t i = done + first; i < bytes; i += stride)
+        dst[i] = src[i];
 }
 
 // Best-fit allocator over one device allocation; free ranges coalesce.
@@ -213,6 +243,7 @@ struct optigpu_server {
     int32_t running = 0;
     optigpu_server_stats stats{};
     std::vector<double> *trace_done = nullptr; // completion times by trace index (replay)
+    int32_t fail_countdown = 0; // testing hook: the step launch that brings it to 0 fails
 };
 
 namespace optigpu {
@@ -307,11 +338,26 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
                              "server: copy in")) != OPTIGPU_OK)
             return st;
     }
+    if (sv->fail_countdown > 0 && --sv->fail_countdown == 0)
+        return fail(OPTIGPU_ERR_CUDA, "server: injected step failure (testing hook)");
     const bool per_call = (sv->flags & OPTIGPU_SERVER_PER_CALL) != 0;
     const uint32_t rflags = sv->flags & OPTIGPU_REDUCE_COMPENSATED;
     if (per_call) {
+        DeviceInfo dev;
+        if ((st = current_device(dev)) != OPTIGPU_OK)
+            return st;
+        auto copy_range = [&](const char *src, char *dst, size_t bytes, const char *what) {
+            const int64_t units = int64_t(bytes + 16 * 256 - 1) / (16 * 256);
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, int64_t(4) * dev.num_sms));
+            copy_range_kernel<<<unsigned(grid), 256, 0, sc.s>>>(src, dst, int64_t(bytes));
+            ++sv->stats.launches;
+            return check_cuda(cudaGetLastError(), what);
+        };
         for (uint64_t tk : adm) {
             const Req &rq = sv->reqs[tk];
+            if (rq.zc_dst && rq.in_bytes &&
+                (st = copy_range(rq.zc_src, base + rq.off_in, rq.in_bytes, "server: gather (per call)")) != OPTIGPU_OK)
+                return st;
             if (rq.r.op == OPTIGPU_OP_TRANSPOSE)
                 st = transpose_dispatch(base + rq.off_in, base + rq.off_out, rq.r.rows, rq.r.cols, rq.r.dtype,
                                         OPTIGPU_TRANSPOSE_AUTO, sc.s);
@@ -320,6 +366,9 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
             if (st != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
+            if (rq.zc_dst && rq.out_bytes &&
+                (st = copy_range(base + rq.off_out, rq.zc_dst, rq.out_bytes, "server: scatter (per call)")) != OPTIGPU_OK)
+                return st;
         }
     } else {
         std::vector<optigpu_desc> descs;
@@ -435,6 +484,28 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
     return OPTIGPU_OK;
 }
 
+// Undoes the admission of `adm` after its launch failed part-way: waits for
+// whatever of the step was already enqueued on its stream (so that no copy or
+// kernel still touches the arena ranges), gives the ranges and slots back and
+// puts the requests back at the head of the queue in their original order.
+void rollback_step(optigpu_server *sv, StreamCtx &sc, const std::vector<uint64_t> &adm)
+{
+    const std::string msg = optigpu_last_error();
+    if (cudaStreamSynchronize(sc.s) != cudaSuccess)
+        cudaGetLastError();
+    for (auto it = adm.rbegin(); it != adm.rend(); ++it) {
+        Req &rq = sv->reqs[*it];
+        sv->arena.release(rq.off_in, rq.in_bytes);
+        sv->arena.release(rq.off_out, rq.out_bytes);
+        rq.state = QUEUED;
+        --sv->running;
+        sv->pending.push_front(*it);
+    }
+    sc.tickets.clear();
+    sc.busy = false;
+    fail(OPTIGPU_ERR_CUDA, msg); // keep the launch's own message as the last error
+}
+
 optigpu_status step_locked(optigpu_server *sv, int32_t *launched)
 {
     if (launched)
@@ -472,8 +543,10 @@ optigpu_status step_locked(optigpu_server *sv, int32_t *launched)
         }
         if (adm.empty())
             break; // out of slots or budget: wait for completions
-        if ((st = launch_step(sv, sc, adm)) != OPTIGPU_OK)
+        if ((st = launch_step(sv, sc, adm)) != OPTIGPU_OK) {
+            rollback_step(sv, sc, adm);
             return st;
+        }
         if (launched)
             ++*launched;
     }
@@ -497,9 +570,12 @@ optigpu_status submit_locked(optigpu_server *sv, const optigpu_request &r, int64
     rq.in_bytes = in_b;
     rq.out_bytes = out_b;
     rq.t_submit = now_s();
-    if (!(sv->flags & OPTIGPU_SERVER_PER_CALL)) {
-        // Pinned host buffers are copied by the step's copy kernels; others by
-        // the copy engines.
+    const bool per_call = (sv->flags & OPTIGPU_SERVER_PER_CALL) != 0;
+    const bool copy_kernels = per_call ? (sv->flags & OPTIGPU_SERVER_COPY_KERNELS) != 0
+                                       : (sv->flags & OPTIGPU_SERVER_COPY_ENGINES) == 0;
+    if (copy_kernels) {
+        // Pinned host buffers are copied by SM copy kernels; others by the
+        // copy engines.
         rq.zc_src = static_cast<const char *>(device_view_of_host(r.host_src, in_b));
         rq.zc_dst = static_cast<char *>(device_view_of_host(r.host_dst, out_b));
         if ((in_b && !rq.zc_src) || !rq.zc_dst)
@@ -548,8 +624,11 @@ optigpu_status optigpu_server_create(size_t mem_budget_bytes, int32_t max_slots,
     *out = nullptr;
     if (mem_budget_bytes < (size_t(1) << 20) || max_slots < 1 || n_streams < 1 || n_streams > 1024)
         return fail(OPTIGPU_ERR_INVALID_ARG, "server: budget >= 1 MiB, max_slots >= 1, n_streams in [1, 1024]");
-    if (flags & ~(OPTIGPU_REDUCE_COMPENSATED | OPTIGPU_SERVER_PER_CALL))
+    if (flags & ~(OPTIGPU_REDUCE_COMPENSATED | OPTIGPU_SERVER_PER_CALL | OPTIGPU_SERVER_COPY_ENGINES |
+                  OPTIGPU_SERVER_COPY_KERNELS))
         return fail(OPTIGPU_ERR_INVALID_ARG, "server: unknown flag bits");
+    if ((flags & OPTIGPU_SERVER_COPY_ENGINES) && (flags & OPTIGPU_SERVER_COPY_KERNELS))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server: COPY_ENGINES and COPY_KERNELS exclude each other");
     optigpu_server *sv = new (std::nothrow) optigpu_server();
     if (!sv)
         return fail(OPTIGPU_ERR_OOM, "server: host allocation failed");
@@ -664,8 +743,11 @@ optigpu_status optigpu_server_replay(optigpu_server *sv, const optigpu_request *
     const double t0 = now_s();
     int64_t next = 0;
     optigpu_status st = OPTIGPU_OK;
+    double prev = 0.0, max_gap = 0.0;
     while (sv->stats.completed - completed0 < count) {
         const double t = now_s() - t0;
+        max_gap = std::max(max_gap, t - prev); // a host stall shows up as one long gap
+        prev = t;
         while (next < count && arrival_s[next] <= t) {
             if ((st = submit_locked(sv, reqs[next], next, nullptr)) != OPTIGPU_OK)
                 break;
@@ -675,6 +757,7 @@ optigpu_status optigpu_server_replay(optigpu_server *sv, const optigpu_request *
             break;
     }
     sv->trace_done = nullptr;
+    sv->stats.replay_max_loop_gap_ns = int64_t(max_gap * 1e9);
     // Replayed tickets are not polled: forget every finished one.
     for (auto it = sv->reqs.begin(); it != sv->reqs.end();)
         it = (it->second.state == DONE && it->second.trace_index >= 0) ? sv->reqs.erase(it) : std::next(it);
@@ -682,6 +765,15 @@ optigpu_status optigpu_server_replay(optigpu_server *sv, const optigpu_request *
         return st;
     for (int64_t i = 0; i < count; ++i)
         latency_s[i] = done[size_t(i)] - (t0 + arrival_s[i]);
+    return OPTIGPU_OK;
+}
+
+optigpu_status optigpu_server_inject_step_failure(optigpu_server *sv, int32_t nth)
+{
+    if (!sv || nth < 0)
+        return fail(OPTIGPU_ERR_INVALID_ARG, "server_inject_step_failure: null server or negative count");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->fail_countdown = nth;
     return OPTIGPU_OK;
 }
 

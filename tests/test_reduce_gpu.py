@@ -99,15 +99,22 @@ def test_float_special_values():
 
 
 def test_compensated_recovers_small_terms():
-    # 1 + many tiny terms: plain FP32 per-thread sums drop them, Neumaier keeps them.
-    n = CHUNK
-    a = np.full(n, 2.0 ** -24, dtype=np.float32)
-    a[::256] = 1.0  # thread 0 of every 256-vector stride sees a 1 first
+    # A 1.0 heads every chunk and 2^-27 fills the rest.  The thread that reads
+    # the 1.0 keeps a running FP32 sum near 1; each of its later 16-byte
+    # vectors of small values sums to 2^-25, under half an ulp of 1, so plain
+    # mode drops all 15 of them (60 * 2^-27 per chunk), while Neumaier's term
+    # keeps them.  Both modes lose the same 3 * 2^-27 per chunk inside the
+    # first vector, whose pairwise tree is plain FP32 in either mode.
+    chunks = 4
+    t = 2.0 ** -27
+    a = np.full(chunks * CHUNK, t, dtype=np.float32)
+    a[::CHUNK] = 1.0
     want = oracle.sum_f64(a)
+    assert want == chunks + (a.size - chunks) * t  # exact in FP64
     got_c = gpu_sum(a, "float32", compensated=True)
     got_p = gpu_sum(a, "float32", compensated=False)
-    assert abs(got_c - want) <= abs(got_p - want)
-    assert abs(got_c - want) <= 1e-7 * oracle.sum_abs_f64(a)
+    assert want - got_p == chunks * 63 * t
+    assert want - got_c == chunks * 3 * t
 
 
 def test_roofline_workload_float32_2p28():
@@ -141,3 +148,42 @@ def test_precision_workload_2p28(dtype):
               f"{err / ref['abs']:.3e} * sum|x|")
         assert err <= REL_TOL * ref["abs"]
     api.stream_status()
+
+
+def test_graph_replay_after_workspace_growth():
+    """A sum captured into a CUDA graph stays correct after a larger sum on the
+    same stream made the library grow that stream's workspace: the workspace
+    the graph was captured with is retired, not freed, so replays still find
+    their counter and partials there."""
+    s = torch.cuda.Stream()
+    small = workloads.vector(3 * CHUNK + 5, "float32", seed=91)
+    # A new workspace holds at least 64 KiB (8160 partials); this sum needs more.
+    big_n = 8200 * CHUNK + 1
+    d_small = to_device(small, "float32")
+    d_big = torch.ones(big_n, dtype=torch.float32, device="cuda")
+    out_g = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    out_b = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s):
+        api.reduce_reserve(small.size)
+        api.reduce_sum(d_small, out=out_g)  # device facts and workspace ready before the capture
+    torch.cuda.synchronize()
+    direct = out_g.item()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        api.reduce_sum(d_small, out=out_g)
+    with torch.cuda.stream(s):
+        api.reduce_sum(d_big, out=out_b)  # needs a larger workspace on the same stream
+    # Churn device memory so that a freed workspace would likely be handed out again.
+    junk = [torch.full((1 << 20,), 7, dtype=torch.int32, device="cuda") for _ in range(8)]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        out_g.fill_(-1.0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert out_g.item() == direct
+    ref = oracle.reduce_reference(small)
+    assert abs(direct - ref["f64"]) <= REL_TOL * ref["abs"]
+    assert out_b.item() == float(big_n)  # ones: every partial and the total are exact
+    with torch.cuda.stream(s):
+        api.stream_status()
+    del junk, g

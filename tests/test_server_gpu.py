@@ -87,11 +87,13 @@ def mixed(seed, count=60, max_side=300, max_len=1 << 18):
     return out, data
 
 
-@pytest.mark.parametrize("per_call,compensated", [(False, False), (False, True), (True, False)])
-def test_served_results_equal_oracle_and_single_calls(per_call, compensated):
+@pytest.mark.parametrize("per_call,compensated,copy", [(False, False, None), (False, True, None),
+                                                        (True, False, None), (False, False, "engines"),
+                                                        (True, False, "kernels")])
+def test_served_results_equal_oracle_and_single_calls(per_call, compensated, copy):
     inst, data = mixed(21)
     sv = api.Server(budget_bytes=256 << 20, max_slots=64, n_streams=3, per_call=per_call,
-                    compensated=compensated)
+                    compensated=compensated, copy=copy)
     reqs = [make_request(i, a) for i, a in zip(inst, data)]
     tickets = [sv.submit(op, s, d) for op, s, d in reqs]
     sv.drain()
@@ -223,5 +225,33 @@ def test_replay_poisson_trace(per_call):
     print(f"per_call={per_call}: p50 {np.percentile(lat, 50) * 1e3:.3f} ms, p99 "
           f"{np.percentile(lat, 99) * 1e3:.3f} ms, steps {st['steps']}, launches {st['launches']}")
     for i, a, (op, s, d) in zip(inst, data, host):
+        check(i, a, op, s, d)
+    sv.close()
+
+
+@pytest.mark.parametrize("per_call,copy", [(False, None), (False, "engines"), (True, None)])
+def test_failed_step_launch_rolls_back_and_retries(per_call, copy):
+    """A step whose launch fails on the host (testing hook, no device fault)
+    leaves nothing behind: its requests return to the queue with their arena
+    space and slots freed, the error reaches the caller, and the next steps
+    serve every request with results equal to the oracle's."""
+    inst, data = mixed(23, count=24)
+    sv = api.Server(budget_bytes=256 << 20, max_slots=16, n_streams=2, per_call=per_call, copy=copy)
+    reqs = [make_request(i, a) for i, a in zip(inst, data)]
+    tickets = [sv.submit(op, s, d) for op, s, d in reqs]
+    sv.inject_step_failure(1)
+    with pytest.raises(api.N.OptigpuError) as e:
+        sv.step()
+    assert "injected" in str(e.value)
+    st = sv.stats()
+    assert st["in_flight"] == 0 and st["bytes_in_use"] == 0 and st["pending"] == len(inst)
+    sv.inject_step_failure(2)  # fails the second launch of a later step() round
+    with pytest.raises(api.N.OptigpuError):
+        sv.drain()
+    sv.drain()
+    assert all(sv.poll(t) for t in tickets)
+    st = sv.stats()
+    assert st["completed"] == len(inst) and st["in_flight"] == 0 and st["bytes_in_use"] == 0
+    for i, a, (op, s, d) in zip(inst, data, reqs):
         check(i, a, op, s, d)
     sv.close()

@@ -3,9 +3,11 @@
 It exists for callers that must not have the library allocate device memory
 (an application whose own pool owns all device memory, a loop that must not
 reach the driver's allocator after start-up, a process held to a hard memory
-budget).  Its result must match optigpu_reduce_sum_ex -- exactly for int32,
-within the 1e-6 * sum|x| tolerance the other sum tests use for floats -- on
-two calls in a row, since every call reuses the same fixed device array.
+budget).  It runs the same kernel with the same chunk partition and
+combine order as optigpu_reduce_sum_ex, so its result must equal that
+entry point's bit for bit, on two calls in a row (every call reuses the same
+fixed device array); both must also match the oracle -- exactly for int32,
+within the 1e-6 * sum|x| tolerance the other sum tests use for floats.
 This file is named to be collected last.
 """
 import ctypes
@@ -50,11 +52,12 @@ def test_noalloc_matches_the_allocating_entry_point(dtype, flags):
         want = _sum(L.optigpu_reduce_sum_ex, d, dtype, flags, stream)
         first = _sum(L.optigpu_reduce_sum_noalloc, d, dtype, flags, stream)
         second = _sum(L.optigpu_reduce_sum_noalloc, d, dtype, flags, stream)
+        assert first == want == second, (n, first, second, want)
         if dtype == "int32":
-            assert first == want == second == oracle.sum_i64(a)
+            assert want == oracle.sum_i64(a)
         else:
-            tol = 1e-6 * oracle.sum_abs_f64(a, dtype) + 1e-300
-            assert abs(first - want) <= tol and abs(second - want) <= tol, (n, first, second, want)
+            ref = oracle.reduce_reference(a, dtype)
+            assert abs(want - ref["f64"]) <= 1e-6 * ref["abs"] + 1e-300, (n, want, ref["f64"])
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
