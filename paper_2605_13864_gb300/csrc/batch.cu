@@ -80,42 +80,58 @@ __device__ __forceinline__ int tile_pitch(int tw)
     return tw <= 2 ? 2 : tw + 2;
 }
 
-// One TH x TW tile (TH * TW <= AREA) of a transpose: coalesced reads of
-// source rows into the shared tile, coalesced writes of destination rows
-// (= tile columns).  Each thread first issues all of its AREA / 256 loads
-// into registers, so they are in flight together.  Edges are predicated.
+// One TH x TW tile (TH * TW <= AREA, TH and TW at most 256) of a transpose:
+// coalesced reads of source rows into the shared tile, coalesced writes of
+// destination rows (= tile columns).  With both sides at most 256, the 256
+// threads stride the tile in whole rows: on the load side thread t always
+// reads tile column t mod TW (rows t / TW + k * 256 / TW), on the store side
+// it always writes tile row t mod TH (columns t / TH + k * 256 / TH).  So a
+// thread's k-th address is its first plus k fixed strides, and its edge
+// tests are one column (row) test plus a row (column) count: a few integer
+// instructions per element instead of a fresh 64-bit index and bound check.
+// Each thread issues all of its AREA / 256 loads before the first shared
+// store, so they are in flight together.
 template <int AREA, typename T>
 __device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t local, T *tile)
 {
     constexpr int PER = AREA / kBatchThreads;
-    const T *src = static_cast<const T *>(in.src);
-    T *dst = static_cast<T *>(in.dst);
     const int th_l = in.th_log2, tw_l = in.tw_log2;
-    const int th = 1 << th_l, tw = 1 << tw_l, area = th << tw_l;
+    const int th = 1 << th_l, tw = 1 << tw_l;
     const int S = tile_pitch<T>(tw);
     const int64_t tr = local / in.aux, tc = local - tr * in.aux;
     const int64_t r0 = tr << th_l, c0 = tc << tw_l;
     const int64_t rows = in.rows, cols = in.cols;
+    const int nr = int(rows - r0 < th ? rows - r0 : th); // rows of the tile inside the matrix
+    const int nc = int(cols - c0 < tw ? cols - c0 : tw); // columns of the tile inside the matrix
+    const int t = threadIdx.x;
+    // Load side: tile column ct, tile rows rt, rt + dr, ...
+    const int ct = t & (tw - 1), rt = t >> tw_l, dr = kBatchThreads >> tw_l;
+    const bool col_in = ct < nc;
+    const T *p = static_cast<const T *>(in.src) + (r0 + rt) * cols + c0 + ct;
+    const int64_t pstep = int64_t(dr) * cols;
     T v[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * kBatchThreads;
-        const int r = e >> tw_l, c = e & (tw - 1);
-        v[k] = (e < area && r0 + r < rows && c0 + c < cols) ? src[(r0 + r) * cols + c0 + c] : T(0);
+        v[k] = (col_in && rt + k * dr < nr) ? *p : T(0);
+        p += pstep;
     }
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * kBatchThreads;
-        if (e < area)
-            tile[(e >> tw_l) * S + (e & (tw - 1))] = v[k];
-    }
+    for (int k = 0; k < PER; ++k)
+        if (col_in && rt + k * dr < nr)
+            tile[(rt + k * dr) * S + ct] = v[k];
     __syncthreads();
+    // Store side: tile row rs (destination column r0 + rs), tile columns
+    // (destination rows c0 + cs) cs, cs + dc, ...
+    const int rs = t & (th - 1), cs = t >> th_l, dc = kBatchThreads >> th_l;
+    const bool row_in = rs < nr;
+    T *q = static_cast<T *>(in.dst) + (c0 + cs) * rows + r0 + rs;
+    const int64_t qstep = int64_t(dc) * rows;
+    const T *sp = tile + rs * S + cs;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * kBatchThreads;
-        const int c = e >> th_l, r = e & (th - 1);
-        if (e < area && c0 + c < cols && r0 + r < rows)
-            dst[(c0 + c) * rows + r0 + r] = tile[r * S + c];
+        if (row_in && cs + k * dc < nc)
+            *q = sp[k * dc];
+        q += qstep;
     }
 }
 
@@ -288,6 +304,8 @@ BatchLayout batch_layout(int64_t count, int64_t items, int64_t chunks)
 
 void batch_tile_shape(int64_t rows, int64_t cols, int area, int &th_log2, int &tw_log2)
 {
+    // Sides are capped at 256 (2^8), which the batch kernel's transpose
+    // relies on (every thread keeps one tile column / row).
     auto log2_ceil = [](int64_t v) {
         int l = 0;
         while ((int64_t(1) << l) < v)
@@ -308,6 +326,8 @@ void batch_tile_shape(int64_t rows, int64_t cols, int area, int &th_log2, int &t
         th_log2 = pr;
         tw_log2 = std::min(pc, a_l - pr);
     }
+    th_log2 = std::min(th_log2, 8);
+    tw_log2 = std::min(tw_log2, 8);
 }
 
 optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, BatchTables &t)
