@@ -949,7 +949,8 @@ def run_gpu(args):
                        "peak_gbs": peak, "peak_kind": peak_kind},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "transpose_tma_kernel<4,64,64,4>", "peak_kind": peak_kind},
+                         "kernel": "transpose_tma_kernel (" + api.tune_configs("transpose", torch.float32)[
+                             api.tune_selected("transpose", torch.float32)] + ")", "peak_kind": peak_kind},
             "components": {
                 "transpose_ms": round(t_avg, 4), "transpose_frac": round(achieved / peak, 4),
                 "transpose_frac_of_8tbs": round(achieved / 8000.0, 4),
@@ -997,6 +998,8 @@ def run_case(args):
     if case.startswith("transpose"):
         dt = torch.bfloat16 if case.endswith("bf16") else torch.float32
         kernel = "tile32" if "tile32" in case else "tma"
+        if args.config is not None:
+            api.tune_select("transpose", dt, args.config)
         m = torch.randn(side, side, device="cuda").to(dt)
         o = torch.empty(side, side, device="cuda", dtype=dt)
         for _ in range(args.case_reps):
@@ -1086,6 +1089,7 @@ def main():
     ap.add_argument("--side", type=int, default=8192)
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--config", type=int, default=None, help="transpose tuner configuration for --case")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -73,10 +73,12 @@ optigpu_status stream_workspace(cudaStream_t stream, size_t bytes, void **ptr, i
 // Kernels may then read and write it directly (over NVLink-C2C on GB300).
 void *device_view_of_host(const void *p, size_t bytes);
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point.
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// shared-memory swizzle unless one is given).
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
-                                    uint32_t box0, uint32_t box1);
+                                    uint32_t box0, uint32_t box1,
+                                    CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE);
 // Same with a third dimension (dim2, stride2_bytes) and a box depth of 1.
 optigpu_status encode_tensor_map_3d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes,

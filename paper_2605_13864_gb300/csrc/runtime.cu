@@ -220,7 +220,7 @@ optigpu_status encode_entry()
 
 optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDataType type,
                                     uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
-                                    uint32_t box0, uint32_t box1)
+                                    uint32_t box0, uint32_t box1, CUtensorMapSwizzle swizzle)
 {
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -239,7 +239,7 @@ optigpu_status encode_tensor_map_2d(CUtensorMap *map, void *base, CUtensorMapDat
     const cuuint32_t box[2] = {box0, box1};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(OPTIGPU_ERR_CUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string(int(r)));

@@ -51,6 +51,42 @@ __device__ __forceinline__ void store_transposed<2>(const uint4 *r, uint32_t out
     }
 }
 
+// Same, with output row j written at row_addr(j) (any layout, e.g. a
+// swizzled one).
+template <int ESIZE, typename RowAddr>
+__device__ __forceinline__ void store_transposed_at(const uint4 *r, RowAddr row_addr)
+{
+    if constexpr (ESIZE == 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            ptx::sts_v4(row_addr(j), make_uint4(word_of(r[0], j), word_of(r[1], j), word_of(r[2], j),
+                                                word_of(r[3], j)));
+    } else {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned sel = h ? 0x7632u : 0x5410u;
+                uint4 o;
+                o.x = __byte_perm(word_of(r[0], w), word_of(r[1], w), sel);
+                o.y = __byte_perm(word_of(r[2], w), word_of(r[3], w), sel);
+                o.z = __byte_perm(word_of(r[4], w), word_of(r[5], w), sel);
+                o.w = __byte_perm(word_of(r[6], w), word_of(r[7], w), sel);
+                ptx::sts_v4(row_addr(2 * w + h), o);
+            }
+        }
+    }
+}
+
+// Byte offset of 16-byte unit `unit` of row `row` in a tile stored as
+// 128-byte-wide boxes (TMA's 128-byte swizzle): rows of `box_rows` 128-byte
+// lines per box, boxes side by side in memory, and inside each 1024-byte
+// group of 8 lines the unit index XORed with the line index mod 8.
+__device__ __forceinline__ uint32_t swz128_offset(uint32_t row, uint32_t unit, uint32_t box_rows)
+{
+    return (unit >> 3) * box_rows * 128u + row * 128u + (((unit & 7u) ^ (row & 7u)) << 4);
+}
+
 template <int ESIZE, int TR, int TC>
 struct TmaTile {
     static constexpr int V = 16 / ESIZE;        // elements per 16-byte vector

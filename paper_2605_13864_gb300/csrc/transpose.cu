@@ -87,6 +87,7 @@ transpose_tile32_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t 
 struct TileOrder {
     int32_t tiles_r, tiles_c, group;
     int64_t tiles_per_mat; // tiles_r * tiles_c; ids run matrix by matrix
+    int32_t rows, cols;    // matrix extent in elements
     __device__ __forceinline__ void coords(int64_t id, int32_t &tr, int32_t &tc, int32_t &b) const
     {
         b = int32_t(id / tiles_per_mat);
@@ -108,7 +109,10 @@ struct TileOrder {
 // stores still read shared memory while the next tile is written.
 // RANK 2: one matrix; RANK 3: a stack of matrices, the batch index being
 // the tensor maps' third coordinate.
-template <int ESIZE, int TR, int TC, int STAGES, int NOB, int RANK = 2>
+// SWZ: tiles move as 128-byte-wide boxes with TMA's 128-byte swizzle (two
+// or more boxes per tile and direction) and the consumers address them
+// through the same XOR pattern; otherwise one box per tile, unswizzled.
+template <int ESIZE, int TR, int TC, int STAGES, int NOB, int RANK = 2, bool SWZ = false>
 __global__ void __launch_bounds__(TmaTile<ESIZE, TR, TC>::THREADS + 32, 1)
 transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
                      const __grid_constant__ CUtensorMap tm_dst, TileOrder order,
@@ -118,8 +122,13 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
     constexpr int V = Tile::V;
     constexpr uint32_t NCONS = Tile::THREADS;
     constexpr uint32_t NWARPS_CONS = NCONS / 32;
+    constexpr int BOX = 128 / ESIZE;          // elements per 128-byte box row (SWZ)
+    constexpr int NS = SWZ ? TC / BOX : 1;    // source boxes per tile
+    constexpr int ND = SWZ ? TR / BOX : 1;    // destination boxes per tile
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t in_base = ptx::smem_addr(smem);
+    // The swizzle pattern repeats every 1024 bytes from a 1024-byte boundary.
+    const uint32_t raw = ptx::smem_addr(smem);
+    const uint32_t in_base = SWZ ? (raw + 1023u) & ~1023u : raw;
     const uint32_t out_base = in_base + STAGES * Tile::BYTES;
     const uint32_t full_bar = out_base + NOB * Tile::BYTES;
     const uint32_t empty_bar = full_bar + 8u * STAGES;
@@ -153,11 +162,20 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
             }
             int32_t tr, tc, b;
             order.coords(first + k * stride, tr, tc, b);
-            ptx::mbar_arrive_expect_tx(full_bar + 8u * s, Tile::BYTES);
-            if (RANK == 3)
-                ptx::tma_load_3d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, b, full_bar + 8u * s);
-            else
-                ptx::tma_load_2d(in_base + s * Tile::BYTES, &tm_src, tc * TC, tr * TR, full_bar + 8u * s);
+            // Swizzled boxes that start past the last column are not loaded
+            // (their elements lie outside the matrix and are never stored).
+            const int ns = SWZ ? min(NS, (order.cols - tc * TC + BOX - 1) / BOX) : 1;
+            ptx::mbar_arrive_expect_tx(full_bar + 8u * s, SWZ ? uint32_t(ns) * TR * 128u : Tile::BYTES);
+#pragma unroll
+            for (int h = 0; h < NS; ++h) {
+                if (h >= ns)
+                    break;
+                const uint32_t dst_smem = in_base + s * Tile::BYTES + uint32_t(h) * TR * 128u;
+                if (RANK == 3)
+                    ptx::tma_load_3d(dst_smem, &tm_src, tc * TC + h * BOX, tr * TR, b, full_bar + 8u * s);
+                else
+                    ptx::tma_load_2d(dst_smem, &tm_src, tc * TC + h * BOX, tr * TR, full_bar + 8u * s);
+            }
         }
         // Before leaving, let every load still in flight land (bounded), so no
         // copy targets this CTA's shared memory after the consumers are gone.
@@ -187,7 +205,9 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
         if (ok) {
 #pragma unroll
             for (int i = 0; i < V; ++i)
-                r[i] = ptx::lds_v4(in_base + s * Tile::BYTES + rd_off + uint32_t(i) * Tile::IN_PITCH);
+                r[i] = ptx::lds_v4(in_base + s * Tile::BYTES +
+                                   (SWZ ? swz128_offset(uint32_t(rb * V + i), uint32_t(cb), TR)
+                                        : rd_off + uint32_t(i) * Tile::IN_PITCH));
         }
         // Output buffer k % NOB is free once the store issued NOB tiles ago
         // has read it: thread 0 (the only thread that issues stores) waits,
@@ -203,7 +223,12 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
             return;
         }
         const uint32_t obuf = out_base + uint32_t(k % NOB) * Tile::BYTES;
-        store_transposed<ESIZE>(r, obuf + wr_off, Tile::OUT_PITCH);
+        if (SWZ)
+            store_transposed_at<ESIZE>(r, [&](int j) {
+                return obuf + swz128_offset(uint32_t(cb * V + j), uint32_t(rb), TC);
+            });
+        else
+            store_transposed<ESIZE>(r, obuf + wr_off, Tile::OUT_PITCH);
         // The values just stored came from stage s, so every lane's read of
         // it is complete: release the stage to the producer, one arrival per
         // warp.
@@ -215,10 +240,16 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
         if (t == 0) {
             int32_t tr, tc, b;
             order.coords(first + k * stride, tr, tc, b);
-            if (RANK == 3)
-                ptx::tma_store_3d(&tm_dst, tr * TR, tc * TC, b, obuf);
-            else
-                ptx::tma_store_2d(&tm_dst, tr * TR, tc * TC, obuf);
+#pragma unroll
+            for (int h = 0; h < ND; ++h) {
+                if (SWZ && tr * TR + h * BOX >= order.rows)
+                    break; // a box wholly past the last destination column: nothing to store
+                const uint32_t src_smem = obuf + uint32_t(h) * TC * 128u;
+                if (RANK == 3)
+                    ptx::tma_store_3d(&tm_dst, tr * TR + h * BOX, tc * TC, b, src_smem);
+                else
+                    ptx::tma_store_2d(&tm_dst, tr * TR + h * BOX, tc * TC, src_smem);
+            }
             ptx::bulk_commit_group();
         }
     }
@@ -235,41 +266,57 @@ struct TmaConfig {
     const void *fn;  // one matrix (2-D tensor maps)
     const void *fn3; // a stack of matrices (3-D tensor maps)
     const char *name;
+    bool swz;        // 128-byte-wide swizzled boxes
 };
 
-template <int ESIZE, int TR, int TC, int STAGES, int NOB>
+template <int ESIZE, int TR, int TC, int STAGES, int NOB, bool SWZ = false>
 TmaConfig make_config(const char *name)
 {
     using Tile = TmaTile<ESIZE, TR, TC>;
+    static_assert(!SWZ || (TR * ESIZE % 128 == 0 && TC * ESIZE % 128 == 0), "swizzled boxes are 128 bytes wide");
     return TmaConfig{ESIZE, TR, TC, STAGES, NOB, Tile::THREADS + 32, Tile::BYTES,
-                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 2>),
-                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 3>), name};
+                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 2, SWZ>),
+                     reinterpret_cast<const void *>(&transpose_tma_kernel<ESIZE, TR, TC, STAGES, NOB, 3, SWZ>), name,
+                     SWZ};
 }
 
 // The compiled TMA configurations per element size; index 0 is the default.
 const std::vector<TmaConfig> &tma_configs(size_t esize)
 {
+    // Index 0, the default: six stages at one CTA per SM, measured fastest
+    // on 16384^2 and 8192^2 (fp32 0.97 of the copy peak against 0.91 for
+    // four stages at two CTAs per SM; deeper rings are slower again).
     static const std::vector<TmaConfig> c4 = {
+        make_config<4, 64, 64, 6, 2>("tma f32 64x64 s6 o2"),
         make_config<4, 64, 64, 4, 2>("tma f32 64x64 s4 o2"),
         make_config<4, 64, 64, 3, 3>("tma f32 64x64 s3 o3"),
         make_config<4, 32, 128, 4, 2>("tma f32 32x128 s4 o2"),
         make_config<4, 128, 32, 4, 2>("tma f32 128x32 s4 o2"),
-        make_config<4, 64, 64, 6, 2>("tma f32 64x64 s6 o2"),
         make_config<4, 32, 64, 6, 3>("tma f32 32x64 s6 o3"),
+        make_config<4, 64, 64, 4, 2, true>("tma f32 64x64 s4 o2 swizzle128"),
+        make_config<4, 64, 64, 5, 2>("tma f32 64x64 s5 o2"),
+        make_config<4, 64, 64, 7, 2>("tma f32 64x64 s7 o2"),
+        make_config<4, 64, 64, 8, 2>("tma f32 64x64 s8 o2"),
     };
     static const std::vector<TmaConfig> c2 = {
+        make_config<2, 64, 128, 6, 2>("tma 16b 64x128 s6 o2"),
         make_config<2, 64, 128, 4, 2>("tma 16b 64x128 s4 o2"),
         make_config<2, 64, 128, 3, 3>("tma 16b 64x128 s3 o3"),
         make_config<2, 128, 64, 4, 2>("tma 16b 128x64 s4 o2"),
         make_config<2, 128, 128, 3, 2>("tma 16b 128x128 s3 o2"),
         make_config<2, 64, 64, 6, 3>("tma 16b 64x64 s6 o3"),
+        make_config<2, 64, 128, 4, 2, true>("tma 16b 64x128 s4 o2 swizzle128"),
+        make_config<2, 64, 128, 5, 2>("tma 16b 64x128 s5 o2"),
+        make_config<2, 64, 128, 7, 2>("tma 16b 64x128 s7 o2"),
+        make_config<2, 64, 128, 8, 2>("tma 16b 64x128 s8 o2"),
     };
     return esize == 4 ? c4 : c2;
 }
 
 size_t tma_smem_bytes(const TmaConfig &c)
 {
-    return size_t(c.stages + c.nob) * c.tile_bytes + size_t(c.stages) * 16;
+    // Swizzled tiles start on a 1024-byte boundary, found inside 1 KiB slack.
+    return size_t(c.stages + c.nob) * c.tile_bytes + size_t(c.stages) * 16 + (c.swz ? 1024 : 0);
 }
 
 // Process-wide choice of TMA configuration per element size (autotuner).
@@ -352,25 +399,31 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
     const TmaConfig &c = configs[size_t(config)];
     const bool rank3 = stack.batch > 1;
     const CUtensorMapDataType type = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    // Box widths: the whole tile row, or 128 bytes with the 128-byte swizzle.
+    const uint32_t box_s = c.swz ? uint32_t(128 / esize) : uint32_t(c.tc);
+    const uint32_t box_d = c.swz ? uint32_t(128 / esize) : uint32_t(c.tr);
+    const CUtensorMapSwizzle swz = c.swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
     alignas(64) CUtensorMap ms, md;
     if (!rank3) {
-        // Source: dim0 = cols (contiguous), dim1 = rows; box TC x TR.
+        // Source: dim0 = cols (contiguous), dim1 = rows; box box_s x TR.
         if ((st = encode_tensor_map_2d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
-                                       uint64_t(lds) * esize, uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
+                                       uint64_t(lds) * esize, box_s, uint32_t(c.tr), swz)) != OPTIGPU_OK)
             return st;
-        // Destination: dim0 = rows (contiguous), dim1 = cols; box TR x TC.
+        // Destination: dim0 = rows (contiguous), dim1 = cols; box box_d x TC.
         if ((st = encode_tensor_map_2d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(ldd) * esize,
-                                       uint32_t(c.tr), uint32_t(c.tc))) != OPTIGPU_OK)
+                                       box_d, uint32_t(c.tc), swz)) != OPTIGPU_OK)
             return st;
     } else {
         // dim2 = the matrix index, strides bs / bd elements.
-        if ((st = encode_tensor_map_3d(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
-                                       uint64_t(stack.batch), uint64_t(lds) * esize, uint64_t(stack.bs) * esize,
-                                       uint32_t(c.tc), uint32_t(c.tr))) != OPTIGPU_OK)
+        if ((st = encode_tensor_map_3d_swizzled(&ms, const_cast<void *>(src), type, uint64_t(cols), uint64_t(rows),
+                                                uint64_t(stack.batch), uint64_t(lds) * esize,
+                                                uint64_t(stack.bs) * esize, box_s, uint32_t(c.tr), swz)) !=
+            OPTIGPU_OK)
             return st;
-        if ((st = encode_tensor_map_3d(&md, dst, type, uint64_t(rows), uint64_t(cols), uint64_t(stack.batch),
-                                       uint64_t(ldd) * esize, uint64_t(stack.bd) * esize, uint32_t(c.tr),
-                                       uint32_t(c.tc))) != OPTIGPU_OK)
+        if ((st = encode_tensor_map_3d_swizzled(&md, dst, type, uint64_t(rows), uint64_t(cols),
+                                                uint64_t(stack.batch), uint64_t(ldd) * esize,
+                                                uint64_t(stack.bd) * esize, box_d, uint32_t(c.tc), swz)) !=
+            OPTIGPU_OK)
             return st;
     }
     const void *fn = rank3 ? c.fn3 : c.fn;
@@ -385,7 +438,7 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
     const size_t smem = tma_smem_bytes(c);
     const uint64_t limit = wait_limit_ns();
     TileOrder order{int32_t(tiles_r), int32_t(tiles_c), std::max(1, std::min(g_group_rows.load(), int(tiles_r))),
-                    per_mat};
+                    per_mat, int32_t(rows), int32_t(cols)};
     void *args[] = {&ms, &md, &order, const_cast<int64_t *>(&num_tiles), const_cast<uint64_t *>(&limit),
                     &dev.status_word};
     return check_cuda(cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(unsigned(c.threads)), args, smem, stream),

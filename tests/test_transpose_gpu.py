@@ -157,6 +157,12 @@ def test_every_compiled_configuration(dtype):
             for r, c in shapes:
                 a = workloads.matrix(r, c, dtype, seed=r + 17 * c + i)
                 check(a, dtype, "auto")
+            # A stack of matrices (3-D tensor maps) through the same configuration.
+            r, c = shapes[1]
+            stack = np.stack([workloads.matrix(r, c, dtype, seed=900 + i + k) for k in range(3)])
+            got = api.transpose_batched(to_device(stack, dtype))
+            want = oracle.transpose_batched(stack)
+            assert np.array_equal(to_host_bits(got), bits(want)), (name, stack.shape)
     finally:
         api.tune_select("transpose", tdt, prev)
 
