@@ -54,8 +54,8 @@ METRIC = "transpose/reduce HBM GB/s (% of GB300 peak); batched+served req/s and 
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
 # TRANSPOSE_SOURCES below).
-NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073798400 + 1028149504,
-                         "src_sha256": "316dfdfc032354f5230c8752f3d1cee90c213ae402953e4e2f9300e8775f75dc"}
+NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073789952 + 1023589888,
+                         "src_sha256": "0453eb65c4e590fc18d0edc21c70ed5f2e2d83e79753dd32484354a3ac9efdab"}
 
 
 def _peaks():
@@ -737,6 +737,11 @@ def measure_paper_sizes(reps: int = 50):
         compact[name] = [entry["l2_resident"]["frac_of_peak"], entry["l2_flushed"]["frac_of_peak"]]
     compact["frac"] = "of peak: [inputs in L2, L2 flushed]"
     compact["sum_2p24_us"] = [round(res["sum_2p24_fp32"][t]["ms"] * 1e3, 2) for t in ("l2_resident", "l2_flushed")]
+    # The floor of this timing method: one 4-byte torch kernel between the
+    # same events (launch, completion and event granularity included).
+    tiny = torch.zeros(1, device="cuda")
+    floor = [round(_median_call_ms(lambda: tiny.add_(1.0), reps, fl) * 1e3, 2) for fl in (None, flush)]
+    res["event_floor_us"] = compact["event_floor_us"] = floor
     res["table_7_4_gbs_rtx5060"] = TABLE_7_4_GBS
     del a, b, v, flush
     torch.cuda.empty_cache()
@@ -1010,6 +1015,15 @@ def run_case(args):
         r = torch.empty((), dtype=torch.float64, device="cuda")
         for _ in range(args.case_reps):
             api.reduce_sum(v, out=r, compensated=case.endswith("comp"))
+    elif case == "batch_transposes":
+        # 64 fp32 1024x1024 transposes through one batch plan (transpose items only).
+        items = [("transpose", torch.randn(1024, 1024, device="cuda"), torch.empty(1024, 1024, device="cuda"))
+                 for _ in range(64)]
+        plan = api.BatchPlan(items)
+        for _ in range(args.case_reps):
+            plan.run()
+        torch.cuda.synchronize()
+        plan.close()
     elif case == "batch":
         inst = workloads.batched_instances(count=args.count)
         data = workloads.batched_data(inst)
@@ -1083,7 +1097,7 @@ def main():
                                                    "as JSON to this path")
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
-                         "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, "
+                         "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, batch_transposes, "
                          "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, histogram, inplace_f32, "
                          "transpose_batched_f32, segmented_f32)")
     ap.add_argument("--side", type=int, default=8192)
