@@ -782,7 +782,10 @@ def measure_next(reps: int = 10):
     del x, y
     m = torch.randn(16384, 16384, device="cuda", generator=g)
     timed("transpose_inplace_16384_fp32", lambda: api.transpose_inplace(m), 2 * m.numel() * 4)
+    mb = m.to(torch.bfloat16)
     del m
+    timed("transpose_inplace_16384_bf16", lambda: api.transpose_inplace(mb), 2 * mb.numel() * 2)
+    del mb
     v = torch.randn(1 << 28, device="cuda", generator=g)
     lens = np.random.default_rng(6).integers(1, 2 * (1 << 28) // 16384, size=16384)
     offs = np.concatenate([[0], np.cumsum(lens)])
@@ -811,6 +814,7 @@ def measure_next(reps: int = 10):
     del v, vi
     torch.cuda.empty_cache()
     short = {"transpose_batched_64x2048x2048_fp32": "stack_64x2048sq", "transpose_inplace_16384_fp32": "inplace_16384sq",
+             "transpose_inplace_16384_bf16": "inplace_16384sq_bf16",
              "reduce_segmented_2p28_fp32_16384seg": "segmented", "reduce_segmented_2p28_fp32_16384seg_planned":
              "segmented_plan", "scan_2p28_fp32": "scan_f32", "scan_2p28_int32_to_int64": "scan_i32_i64",
              "scan_2p28_bf16_to_fp32": "scan_bf16_f32", "histogram_2p28_int32_4096bins": "histogram"}
@@ -1054,8 +1058,8 @@ def run_case(args):
         v = torch.randint(0, 4096, (side * side,), dtype=torch.int32, device="cuda")
         for _ in range(args.case_reps):
             api.histogram(v, 0, 1, 4096)
-    elif case == "inplace_f32":
-        m = torch.randn(side, side, device="cuda")
+    elif case in ("inplace_f32", "inplace_bf16"):
+        m = torch.randn(side, side, device="cuda").to(torch.bfloat16 if case.endswith("bf16") else torch.float32)
         for _ in range(args.case_reps):
             api.transpose_inplace(m)
     elif case == "transpose_batched_f32":
@@ -1098,7 +1102,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, batch_transposes, "
-                         "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, histogram, inplace_f32, "
+                         "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, histogram, inplace_f32, inplace_bf16, "
                          "transpose_batched_f32, segmented_f32)")
     ap.add_argument("--side", type=int, default=8192)
     ap.add_argument("--count", type=int, default=1024)

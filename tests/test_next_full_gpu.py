@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import require_gpu, to_device, torch
+from gpu_util import require_gpu, to_device, to_host_bits, torch
 from paper_2605_13864_gb300 import api, workloads
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +56,19 @@ def test_transpose_inplace_16384_float32():
     got = d.cpu().numpy()
     del d
     assert np.array_equal(got.view(np.uint32), oracle.transpose(a).view(np.uint32))
+
+
+def test_transpose_inplace_16384_bfloat16():
+    """The 16-bit in-place path (128 x 128 tile pairs) on the full square."""
+    n = 16384
+    a = workloads.matrix(n, n, "bfloat16", seed=74)
+    d = to_device(a, "bfloat16")
+    api.transpose_inplace(d)
+    torch.cuda.synchronize()
+    api.stream_status()
+    got = to_host_bits(d)
+    del d
+    assert np.array_equal(got, oracle.transpose(a))
 
 
 def test_segmented_2p28_float32_16384_segments():

@@ -113,7 +113,7 @@ def test_reduce_segmented_back_to_back_calls():
 
 
 @pytest.mark.parametrize("dtype", ["float32", "bfloat16", "int32"])
-@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128, 200, 1000, 4100])
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128, 200, 392, 1000, 2048, 4100])
 def test_transpose_inplace(dtype, n):
     a = workloads.matrix(n, n, dtype, seed=n)
     d = to_device(a, dtype)
