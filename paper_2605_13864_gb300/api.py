@@ -30,8 +30,13 @@ def _stream_ptr(stream) -> int:
 
 
 def transpose(src: torch.Tensor, out: torch.Tensor | None = None, kernel: str = "auto",
-              stream=None) -> torch.Tensor:
-    """``out[c, r] = src[r, c]`` (thesis Listing 3.5: out[x][y] = in[y][x])."""
+              stream=None, blocking: bool = True) -> torch.Tensor:
+    """``out[c, r] = src[r, c]`` (thesis Listing 3.5: out[x][y] = in[y][x]).
+
+    For host tensors the call waits for the result unless ``blocking`` is
+    False; then ``out`` is complete once ``stream`` (default: the current
+    stream) has been synchronized, and both tensors must stay alive until
+    then."""
     if src.dim() != 2:
         raise ValueError("transpose expects a 2-D tensor")
     if not src.is_cuda:
@@ -47,7 +52,8 @@ def transpose(src: torch.Tensor, out: torch.Tensor | None = None, kernel: str = 
                                             host.data_ptr() if host.numel() else None, rows, cols,
                                             dtype_code(src.dtype), int(s.cuda_stream))
         N.check(st, "optigpu_transpose_host")
-        s.synchronize()
+        if blocking:
+            s.synchronize()
         return host
     if not src.is_contiguous():
         raise ValueError("transpose expects a contiguous (row-major) source")
@@ -92,11 +98,13 @@ def transpose_batched(src: torch.Tensor, out: torch.Tensor | None = None, stream
 
 
 def reduce_sum(x: torch.Tensor, compensated: bool = False, out: torch.Tensor | None = None,
-               stream=None) -> torch.Tensor:
+               stream=None, blocking: bool = True) -> torch.Tensor:
     """Sum of all elements (thesis Listing 2.1: reduce_sum(N, A)).
 
     Returns a 0-d int64 tensor for int32 input and a 0-d float64 tensor for
-    float input (the partials are combined in FP64 on the GPU).
+    float input (the partials are combined in FP64 on the GPU).  For a host
+    tensor the call waits for the result unless ``blocking`` is False (then
+    synchronize ``stream`` before reading it).
     """
     if not x.is_cuda:
         # Host buffer: the library pipelines the copy-in against the partials.
@@ -109,7 +117,8 @@ def reduce_sum(x: torch.Tensor, compensated: bool = False, out: torch.Tensor | N
         st = N.lib().optigpu_reduce_sum_host(x.data_ptr() if x.numel() else None, x.numel(),
                                              dtype_code(x.dtype), res.data_ptr(), flags, int(s.cuda_stream))
         N.check(st, "optigpu_reduce_sum_host")
-        s.synchronize()
+        if blocking:
+            s.synchronize()
         return res
     if not x.is_contiguous():
         raise ValueError("reduce_sum expects a contiguous tensor")

@@ -99,3 +99,27 @@ def test_transpose_host_pinned_and_pageable_agree():
     out = torch.empty((2050, 4100), dtype=torch.float32)
     api.transpose(host(a, "float32", pin=False), out=out)
     assert torch.equal(pinned.view(torch.int32), out.view(torch.int32))
+
+
+@pytest.mark.parametrize("pin", [True, False])
+def test_concurrent_non_blocking_transpose_and_sum(pin):
+    """A host-buffer transpose and a host-buffer sum issued without waiting on
+    two streams (the benchmark's end-to-end step) both give the oracle's
+    result once the streams are synchronized."""
+    s_t, s_r = torch.cuda.Stream(), torch.cuda.Stream()
+    m = workloads.matrix(1031, 2053, "float32", seed=31)
+    v = workloads.vector((1 << 23) + 17, "float32", seed=32)
+    hm, hv = host(m, "float32", pin=pin), host(v, "float32", pin=pin)
+    out_t = torch.empty((2053, 1031), dtype=torch.float32)
+    out_r = torch.empty((), dtype=torch.float64)
+    if pin:
+        out_t, out_r = out_t.pin_memory(), out_r.pin_memory()
+    for _ in range(2):
+        api.transpose(hm, out=out_t, stream=s_t, blocking=False)
+        api.reduce_sum(hv, out=out_r, stream=s_r, blocking=False)
+        s_t.synchronize()
+        s_r.synchronize()
+        assert np.array_equal(out_t.numpy().view(np.uint32), oracle.transpose(m).view(np.uint32))
+        ref = oracle.reduce_reference(v)
+        assert abs(out_r.item() - ref["f64"]) <= 1e-6 * ref["abs"]
+        assert out_r.item() == api.reduce_sum(to_device(v, "float32")).item()
