@@ -1013,7 +1013,7 @@ def run_case(args):
 
     torch.cuda.set_device(0)
     side, case = args.side, args.case
-    if case.startswith("transpose"):
+    if case.startswith("transpose") and not case.startswith("transpose_batched"):
         dt = torch.bfloat16 if case.endswith("bf16") else torch.float32
         kernel = "tile32" if "tile32" in case else "tma"
         if args.config is not None:
