@@ -40,7 +40,7 @@ static_assert(sizeof(BatchInst) % 8 == 0 && alignof(BatchInst) >= 8, "descriptor
 template <int AREA>
 struct BatchShared {
     union {
-        uint32_t tile[AREA + AREA / 2];
+        uint32_t tile[AREA > 0 ? AREA + AREA / 2 : 1]; // AREA 0: sums only, no transpose tile
         ReduceCore<OPTIGPU_INT32, false>::Shared ri;
         ReduceCore<OPTIGPU_FLOAT32, false>::Shared rf;
         ReduceCore<OPTIGPU_FLOAT32, true>::Shared rfc;
@@ -135,11 +135,11 @@ __device__ __forceinline__ void transpose_tile(const BatchInst &in, int64_t loca
     }
 }
 
-template <int DT, bool COMP, typename Sh>
+template <int DT, bool COMP, int MB, typename Sh>
 __device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local, uint32_t inst, void *partials,
                                              unsigned *inst_done, Sh &sh, int &s_last)
 {
-    using Core = ReduceCore<DT, COMP>;
+    using Core = ReduceCore<DT, COMP, MB>;
     using P = typename Core::Partial;
     auto &rs = *reinterpret_cast<typename Core::Shared *>(&sh);
     P *mine = static_cast<P *>(partials) + in.aux;
@@ -171,12 +171,17 @@ __device__ __forceinline__ void reduce_chunk(const BatchInst &in, int64_t local,
 // i runs, thread 0 claims item i+3, and warp 0 copies item i+2's instance
 // index and item i+1's descriptor into the shared ring (cp.async), all
 // completed by the barrier that ends item i.
-template <int AREA>
-__global__ void __launch_bounds__(kBatchThreads, 4)
+// SUMS: a batch of sums only (every item a chunk).  No transpose tile in
+// shared memory and the sum's 4-loads-in-flight schedule: 48 registers, 5
+// CTAs per SM instead of 4 (6 would spill); the arithmetic, and so every
+// result, is the same.
+template <int AREA, bool SUMS = false>
+__global__ void __launch_bounds__(kBatchThreads, SUMS ? 5 : 4)
 batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ item_inst, int64_t total_items,
              unsigned long long *queue, unsigned *inst_done, void *partials, int compensated)
 {
-    __shared__ BatchShared<AREA> sh;
+    constexpr int MB = SUMS ? 4 : 8;
+    __shared__ BatchShared<SUMS ? 0 : AREA> sh;
     const int t = threadIdx.x, lane = t & 31;
     if (t == 0) {
         int64_t prev = 0;
@@ -215,33 +220,36 @@ batch_kernel(const BatchInst *__restrict__ insts, const uint32_t *__restrict__ i
         const uint32_t inst = sh.iidx[cur];
         const int64_t local = item - in.first_item;
         if (in.op == OPTIGPU_OP_TRANSPOSE) {
-            if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
-                transpose_tile<AREA, uint16_t>(in, local, reinterpret_cast<uint16_t *>(sh.u.tile));
-            else
-                transpose_tile<AREA, uint32_t>(in, local, sh.u.tile);
+            // (Never reached with SUMS: such batches hold no transpose item.)
+            if constexpr (!SUMS) {
+                if (in.dtype == OPTIGPU_BFLOAT16 || in.dtype == OPTIGPU_FLOAT16)
+                    transpose_tile<AREA, uint16_t>(in, local, reinterpret_cast<uint16_t *>(sh.u.tile));
+                else
+                    transpose_tile<AREA, uint32_t>(in, local, sh.u.tile);
+            }
         } else {
             switch (in.dtype * 2 + (compensated ? 1 : 0)) {
             case OPTIGPU_INT32 * 2:
             case OPTIGPU_INT32 * 2 + 1:
-                reduce_chunk<OPTIGPU_INT32, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_INT32, false, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             case OPTIGPU_FLOAT32 * 2:
-                reduce_chunk<OPTIGPU_FLOAT32, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_FLOAT32, false, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             case OPTIGPU_FLOAT32 * 2 + 1:
-                reduce_chunk<OPTIGPU_FLOAT32, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_FLOAT32, true, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             case OPTIGPU_BFLOAT16 * 2:
-                reduce_chunk<OPTIGPU_BFLOAT16, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_BFLOAT16, false, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             case OPTIGPU_BFLOAT16 * 2 + 1:
-                reduce_chunk<OPTIGPU_BFLOAT16, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_BFLOAT16, true, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             case OPTIGPU_FLOAT16 * 2:
-                reduce_chunk<OPTIGPU_FLOAT16, false>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_FLOAT16, false, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             default:
-                reduce_chunk<OPTIGPU_FLOAT16, true>(in, local, inst, partials, inst_done, sh.u, sh.last);
+                reduce_chunk<OPTIGPU_FLOAT16, true, MB>(in, local, inst, partials, inst_done, sh.u, sh.last);
                 break;
             }
         }
@@ -376,21 +384,37 @@ optigpu_status batch_tables(const optigpu_desc *descs, int32_t count, int area, 
     return OPTIGPU_OK;
 }
 
+namespace {
+std::mutex g_occ_mu;
+std::map<std::pair<int, const void *>, int> g_occ; // (device, kernel) -> resident CTAs per SM
+} // namespace
+
 optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
                             unsigned long long *d_queue, unsigned *d_done, int64_t clear_done, void *d_partials,
-                            int compensated, cudaStream_t stream, int *grid_out)
+                            int compensated, cudaStream_t stream, int *grid_out, bool sums_only)
 {
     const BatchConfig &c = batch_configs()[size_t(config)];
+    // A batch of sums only runs the kernel form without a transpose tile, at
+    // as many CTAs per SM as fit; the configuration's tile and CTA cap are
+    // for batches that hold transposes.
+    const void *fn = sums_only ? reinterpret_cast<const void *>(&batch_kernel<4096, true>) : c.fn;
     DeviceInfo dev;
     optigpu_status st = current_device(dev);
     if (st != OPTIGPU_OK)
         return st;
     int per_sm = 0;
-    if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.fn, kBatchThreads, 0),
-                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)")) != OPTIGPU_OK)
-        return st;
-    per_sm = std::max(per_sm, 1);
-    if (c.ctas_per_sm > 0)
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find({dev.device, fn});
+        if (it == g_occ.end()) {
+            if ((st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, 0),
+                                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)")) != OPTIGPU_OK)
+                return st;
+            it = g_occ.emplace(std::make_pair(dev.device, fn), std::max(per_sm, 1)).first;
+        }
+        per_sm = it->second;
+    }
+    if (!sums_only && c.ctas_per_sm > 0)
         per_sm = std::min(per_sm, c.ctas_per_sm);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(per_sm) * dev.num_sms));
     // The counters follow the queue in the layout (batch_layout), so one
@@ -403,7 +427,7 @@ optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t
         return st;
     int comp = compensated;
     void *args[] = {&d_insts, &d_item_inst, &items, &d_queue, &d_done, &d_partials, &comp};
-    if ((st = check_cuda(cudaLaunchKernel(c.fn, dim3(unsigned(grid)), dim3(kBatchThreads), args, 0, stream),
+    if ((st = check_cuda(cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(kBatchThreads), args, 0, stream),
                          "launch batch kernel")) != OPTIGPU_OK)
         return st;
     if (grid_out)
@@ -495,7 +519,8 @@ void free_plan_device(optigpu_batch_plan *p)
 optigpu_status enqueue_run(optigpu_batch_plan *p, int config, cudaStream_t stream, int *grid_out)
 {
     return batch_launch(config, p->d_insts, p->d_item_inst, p->total_items, p->d_queue, p->d_inst_done, 0,
-                        p->d_partials, (p->flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, stream, grid_out);
+                        p->d_partials, (p->flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, stream, grid_out,
+                        p->total_items == p->total_chunks);
 }
 
 // Builds the device tables of `p` for its current configuration (tile size).
@@ -900,5 +925,5 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
         return st;
     // The table kernel zeroed the queue and the counters (clear_done < 0).
     return batch_launch(config, d_insts, d_items, items, d_queue, d_done, -1, base + L.off_part,
-                        (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr);
+                        (flags & OPTIGPU_REDUCE_COMPENSATED) ? 1 : 0, s, nullptr, true);
 }

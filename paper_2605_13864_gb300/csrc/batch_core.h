@@ -69,8 +69,10 @@ int batch_tile(int config);
 // at zero and are left at zero by every run, pass 0.  A negative `clear_done`
 // means the caller has already zeroed the queue and the counters in work
 // ordered before this launch on `stream`, so nothing is reset here.
+// `sums_only` (every item is a sum chunk) selects the kernel form without a
+// transpose tile, which fits more CTAs on an SM; results are the same.
 optigpu_status batch_launch(int config, const BatchInst *d_insts, const uint32_t *d_item_inst, int64_t items,
                             unsigned long long *d_queue, unsigned *d_done, int64_t clear_done, void *d_partials,
-                            int compensated, cudaStream_t stream, int *grid_out);
+                            int compensated, cudaStream_t stream, int *grid_out, bool sums_only);
 
 } // namespace optigpu

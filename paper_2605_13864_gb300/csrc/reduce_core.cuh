@@ -98,17 +98,19 @@ struct ElemTraits<OPTIGPU_FLOAT16> {
     }
 };
 
-// Builds the 16-byte vector `vi` of the chunk starting at element `base`
-// from scalar reads; elements at or past n are zero bits.
+// Builds a 16-byte vector of a chunk from scalar reads: its elements are
+// chunk[first .. first + V), where `chunk` points at the chunk's first
+// element and `rem` elements of the chunk lie before n; elements at or past
+// rem are zero bits.  32-bit offsets inside the chunk (at most 16384).
 template <int DT>
-__device__ __forceinline__ uint4 gather_vector(const void *src, int64_t n, int64_t first)
+__device__ __forceinline__ uint4 gather_vector(const void *chunk, int rem, int first)
 {
     constexpr int V = ElemTraits<DT>::V;
     uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-        const int64_t i = first + e;
-        const uint32_t b = i < n ? ElemTraits<DT>::scalar_bits(src, i) : 0u;
+        const int i = first + e;
+        const uint32_t b = i < rem ? ElemTraits<DT>::scalar_bits(chunk, i) : 0u;
         if (V == 4)
             w[e] = b;
         else
@@ -261,21 +263,22 @@ struct ReduceCore {
             // gathered from scalar reads.  A batch's reads are all issued
             // before any is added, so they are in flight together; vectors
             // that start at or past n are not added (as in the full path,
-            // where none exist).
+            // where none exist).  Offsets are 32-bit and relative to the
+            // chunk, so each element costs a compare and a load.
+            const char *chunk = static_cast<const char *>(src) + base * int64_t(16 / V);
+            const int rem = n - base < kReduceChunk ? int(n - base) : int(kReduceChunk);
 #pragma unroll
             for (int k0 = 0; k0 < VPT; k0 += BATCH) {
                 uint4 buf[BATCH];
 #pragma unroll
                 for (int u = 0; u < BATCH; ++u) {
-                    const int64_t first = base + int64_t((k0 + u) * kReduceThreads + t) * V;
-                    buf[u] = first < n ? gather_vector<DT>(src, n, first) : make_uint4(0u, 0u, 0u, 0u);
+                    const int first = ((k0 + u) * kReduceThreads + t) * V;
+                    buf[u] = first < rem ? gather_vector<DT>(chunk, rem, first) : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
-                for (int u = 0; u < BATCH; ++u) {
-                    const int64_t first = base + int64_t((k0 + u) * kReduceThreads + t) * V;
-                    if (first < n)
+                for (int u = 0; u < BATCH; ++u)
+                    if (((k0 + u) * kReduceThreads + t) * V < rem)
                         acc.add(T::vec_sum(buf[u]));
-                }
             }
         }
         return to_partial(block_combine(acc, sh));

@@ -455,7 +455,7 @@ optigpu_status launch_step(optigpu_server *sv, StreamCtx &sc, const std::vector<
             if ((st = batch_launch(config, reinterpret_cast<BatchInst *>(ws + L.off_inst),
                                    reinterpret_cast<uint32_t *>(ws + L.off_items), t.items, d_queue, d_done,
                                    gather_clears ? -1 : int64_t(descs.size()), ws + off_part, rflags ? 1 : 0,
-                                   sc.s, nullptr)) != OPTIGPU_OK)
+                                   sc.s, nullptr, t.items == t.chunks)) != OPTIGPU_OK)
                 return st;
             ++sv->stats.launches;
         }
