@@ -986,7 +986,9 @@ def run_gpu(args):
         # records go to --detail.  The batched and served summaries come
         # last, so that a reader of the line's tail sees them.
         detail = {}
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
+            # The host oracle is timed at N = 1 only (at N > 1 every rank's host
+            # cores serve a GPU replica).
             line["cpu_baseline"] = cpu_baseline(mat_h, vec_h, args.cpu_seconds)
         del mat_h, vec_h
         parts = [("small", args.no_small, measure_small), ("paper_sizes", args.no_paper_sizes, measure_paper_sizes),
