@@ -967,8 +967,8 @@ def run_gpu(args):
                        "peak_gbs": peak, "peak_kind": peak_kind},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "transpose_tma_kernel (" + api.tune_configs("transpose", torch.float32)[
-                             api.tune_selected("transpose", torch.float32)] + ")", "peak_kind": peak_kind},
+                         "kernel": "transpose_tma_kernel (" + api.transpose_config_for(ROWS, COLS)[1] + ")",
+                         "peak_kind": peak_kind},
             "components": {
                 "transpose_ms": round(t_avg, 4), "transpose_frac": round(achieved / peak, 4),
                 "transpose_frac_of_8tbs": round(achieved / 8000.0, 4),

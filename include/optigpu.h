@@ -143,6 +143,13 @@ int optigpu_transpose_tma_eligible(const void *src, const void *dst,
                                    int64_t rows, int64_t cols,
                                    optigpu_dtype dtype);
 
+/* Index (see optigpu_tune_config_name) of the concrete transpose
+ * configuration AUTO launches for a rows x cols matrix of dtype, assuming
+ * 16-byte aligned pointers: the selected configuration, with the default
+ * "by size" entry resolved by the bytes the call moves.  -1 for a bad dtype
+ * or a negative size. */
+int optigpu_transpose_config_for(int64_t rows, int64_t cols, optigpu_dtype dtype);
+
 /* ------------------------------------------------------------------------ */
 /* Sum reduction (Listing 2.1, Sec. 2.1; partial-sum form Listing 2.2)      */
 /* ------------------------------------------------------------------------ */
@@ -462,7 +469,9 @@ void optigpu_server_destroy(optigpu_server *server);
 
 
 /* Number of configurations of `op` for `dtype` (-1 for a bad op or dtype).
- * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel.
+ * Transpose: indices 0 .. n-2 are TMA kernels, n-1 the padded tile32 kernel;
+ * index 0, the default, picks between indices 1 and 2 by the bytes a call
+ * moves (optigpu_transpose_config_for tells which).
  * OPTIGPU_OP_BATCH ignores `dtype`; its selection is the default of new
  * plans.  OPTIGPU_OP_SCAN ignores `dtype`: 0 = single pass (carries used
  * one chunk later), 1 = three passes, 2 = single pass (carries read at once). */

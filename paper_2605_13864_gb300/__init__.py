@@ -10,5 +10,5 @@ does, and raises if the library cannot be built or loaded.
 """
 from ._native import OptigpuError, load  # noqa: F401
 from .api import (BatchPlan, Server, autotune, histogram, reduce_reserve, reduce_segmented, reduce_sum, scan, release_workspaces,  # noqa: F401
-                  set_wait_limit_ns, stream_status, tma_eligible, transpose, transpose_batched, transpose_inplace, tune_configs,
+                  set_wait_limit_ns, stream_status, tma_eligible, transpose, transpose_batched, transpose_config_for, transpose_inplace, tune_configs,
                   tune_select, tune_selected)

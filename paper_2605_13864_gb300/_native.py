@@ -45,6 +45,7 @@ SIGNATURES = {
     "optigpu_transpose": (_ci, [_vp, _vp, _i64, _i64, _ci, _vp]),
     "optigpu_transpose_ex": (_ci, [_vp, _vp, _i64, _i64, _ci, _ci, _vp]),
     "optigpu_transpose_tma_eligible": (_ci, [_vp, _vp, _i64, _i64, _ci]),
+    "optigpu_transpose_config_for": (_ci, [_i64, _i64, _ci]),
     "optigpu_transpose_strided": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _ci, _vp]),
     "optigpu_transpose_batched": (_ci, [_vp, _i64, _vp, _i64, _i64, _i64, _i64, _ci, _vp]),
     "optigpu_transpose_inplace": (_ci, [_vp, _i64, _ci, _vp]),

@@ -187,6 +187,13 @@ def reduce_segmented(x: torch.Tensor, offsets, compensated: bool = False, stream
     return out
 
 
+def transpose_config_for(rows: int, cols: int, dtype: torch.dtype = torch.float32) -> tuple[int, str]:
+    """(index, name) of the configuration AUTO launches for an aligned
+    rows x cols matrix of ``dtype``."""
+    i = int(N.lib().optigpu_transpose_config_for(int(rows), int(cols), dtype_code(dtype)))
+    return i, tune_configs("transpose", dtype)[i]
+
+
 def tma_eligible(src: torch.Tensor, dst: torch.Tensor) -> bool:
     rows, cols = src.shape
     return bool(N.lib().optigpu_transpose_tma_eligible(src.data_ptr(), dst.data_ptr(), rows, cols,

@@ -283,10 +283,17 @@ TmaConfig make_config(const char *name)
 // The compiled TMA configurations per element size; index 0 is the default.
 const std::vector<TmaConfig> &tma_configs(size_t esize)
 {
-    // Index 0, the default: six stages at one CTA per SM, measured fastest
-    // on 16384^2 and 8192^2 (fp32 0.97 of the copy peak against 0.91 for
-    // four stages at two CTAs per SM; deeper rings are slower again).
+    // Index 0, the default, is chosen by size (kBySize): measured with CUDA
+    // events on square fp32 and bf16 matrices (fraction of the copy peak,
+    // inputs cold / left in L2 by the previous call), four stages at two CTAs
+    // per SM win below 1 GiB moved (fp32 5120^2-10240^2: 0.94-0.96 / 0.78-0.89,
+    // bf16 6144^2-12288^2: 0.93-0.96 / 0.78-0.86), six stages at one CTA per SM
+    // from 1 GiB up (fp32 12288^2 0.954 / 0.954 against 0.944 / 0.900, 16384^2
+    // 0.968 against 0.91; bf16 16384^2 0.938 against 0.925).  Entry 0 carries
+    // the six-stage kernel; launch_tma resolves it by size.  Deeper rings
+    // (7-12 stages) and the other shapes measured slower.
     static const std::vector<TmaConfig> c4 = {
+        make_config<4, 64, 64, 6, 2>("tma f32 64x64 by size (s4 o2 below 1 GiB moved, s6 o2 from 1 GiB)"),
         make_config<4, 64, 64, 6, 2>("tma f32 64x64 s6 o2"),
         make_config<4, 64, 64, 4, 2>("tma f32 64x64 s4 o2"),
         make_config<4, 64, 64, 3, 3>("tma f32 64x64 s3 o3"),
@@ -299,6 +306,7 @@ const std::vector<TmaConfig> &tma_configs(size_t esize)
         make_config<4, 64, 64, 8, 2>("tma f32 64x64 s8 o2"),
     };
     static const std::vector<TmaConfig> c2 = {
+        make_config<2, 64, 128, 6, 2>("tma 16b 64x128 by size (s4 o2 below 1 GiB moved, s6 o2 from 1 GiB)"),
         make_config<2, 64, 128, 6, 2>("tma 16b 64x128 s6 o2"),
         make_config<2, 64, 128, 4, 2>("tma 16b 64x128 s4 o2"),
         make_config<2, 64, 128, 3, 3>("tma 16b 64x128 s3 o3"),
@@ -311,6 +319,17 @@ const std::vector<TmaConfig> &tma_configs(size_t esize)
         make_config<2, 64, 128, 8, 2>("tma 16b 64x128 s8 o2"),
     };
     return esize == 4 ? c4 : c2;
+}
+
+// Configuration 0 picks one of two entries by the bytes a call moves.
+constexpr int kBySize = 0, kDeepRing = 1, kShallowRing = 2;
+constexpr uint64_t kBySizeThreshold = uint64_t(1) << 30; // bytes read + written
+
+int resolve_tma_config(int config, uint64_t moved_bytes)
+{
+    if (config != kBySize)
+        return config;
+    return moved_bytes < kBySizeThreshold ? kShallowRing : kDeepRing;
 }
 
 size_t tma_smem_bytes(const TmaConfig &c)
@@ -396,6 +415,7 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
         config = g_tma_choice[esize == 4 ? 0 : 1].load();
     if (config < 0 || config >= int(configs.size()))
         return fail(OPTIGPU_ERR_INVALID_ARG, "transpose: unknown TMA configuration");
+    config = resolve_tma_config(config, 2 * uint64_t(rows) * uint64_t(cols) * uint64_t(stack.batch) * esize);
     const TmaConfig &c = configs[size_t(config)];
     const bool rank3 = stack.batch > 1;
     const CUtensorMapDataType type = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
@@ -650,6 +670,20 @@ int optigpu_transpose_tma_eligible(const void *src, const void *dst, int64_t row
     if (!dtype_valid(int(dtype)))
         return 0;
     return tma_eligible(src, dst, rows, cols, cols, rows, esize_of(dtype)) ? 1 : 0;
+}
+
+int optigpu_transpose_config_for(int64_t rows, int64_t cols, optigpu_dtype dtype)
+{
+    if (!dtype_valid(int(dtype)) || rows < 0 || cols < 0)
+        return -1;
+    const size_t es = esize_of(dtype);
+    const int64_t per16 = int64_t(16 / es);
+    const int tile32 = int(tma_configs(es).size());
+    const int choice = transpose_selected(es);
+    if (choice >= tile32 || rows == 0 || cols == 0 || rows % per16 || cols % per16 || rows > (int64_t(1) << 30) ||
+        cols > (int64_t(1) << 30))
+        return choice >= tile32 ? choice : tile32;
+    return resolve_tma_config(choice, 2 * uint64_t(rows) * uint64_t(cols) * es);
 }
 
 } // extern "C"

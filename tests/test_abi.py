@@ -274,3 +274,26 @@ def test_histogram_validation(lib):
     assert f(FAKE, 10, 0, 1, 4, FAKE + 4, None) == N.ERR_INVALID_ARG    # counts misaligned
     assert f(FAKE + 2, 10, 0, 1, 4, FAKE, None) == N.ERR_INVALID_ARG    # src misaligned
     assert f(FAKE, 10, 1 << 41, 1, 4, FAKE, None) == N.ERR_INVALID_ARG
+
+
+def test_transpose_default_configuration_is_chosen_by_size(lib):
+    """Configuration 0 (the default) launches the four-stage ring below 1 GiB
+    moved and the six-stage ring from 1 GiB up; an explicit selection is
+    launched as selected."""
+    names = [lib.optigpu_tune_config_name(N.OP_TRANSPOSE, N.FLOAT32, i).decode() for i in range(3)]
+    assert "by size" in names[0] and names[1].endswith("s6 o2") and names[2].endswith("s4 o2")
+    prev = lib.optigpu_tune_selected(N.OP_TRANSPOSE, N.FLOAT32)
+    try:
+        assert lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 0) == N.OK
+        assert lib.optigpu_transpose_config_for(16384, 16384, N.FLOAT32) == 1   # 2 GiB moved
+        assert lib.optigpu_transpose_config_for(8192, 16384, N.FLOAT32) == 1    # exactly 1 GiB
+        assert lib.optigpu_transpose_config_for(8192, 8192, N.FLOAT32) == 2     # 512 MiB
+        assert lib.optigpu_transpose_config_for(16384, 16384, N.BFLOAT16) == 1  # 1 GiB of bf16
+        assert lib.optigpu_transpose_config_for(12288, 12288, N.BFLOAT16) == 2
+        n = lib.optigpu_tune_num_configs(N.OP_TRANSPOSE, N.FLOAT32)
+        assert lib.optigpu_transpose_config_for(30, 16384, N.FLOAT32) == n - 1   # rows not a multiple of 4: tile32
+        assert lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, 3) == N.OK
+        assert lib.optigpu_transpose_config_for(8192, 8192, N.FLOAT32) == 3
+        assert lib.optigpu_transpose_config_for(-1, 8, N.FLOAT32) == -1
+    finally:
+        lib.optigpu_tune_select(N.OP_TRANSPOSE, N.FLOAT32, prev)
