@@ -54,8 +54,8 @@ METRIC = "transpose/reduce HBM GB/s (% of GB300 peak); batched+served req/s and 
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
 # TRANSPOSE_SOURCES below).
-NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073789952 + 1023589888,
-                         "src_sha256": "0453eb65c4e590fc18d0edc21c70ed5f2e2d83e79753dd32484354a3ac9efdab"}
+NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073772800 + 1024100096,
+                         "src_sha256": "b84e73f642bf287d525d0f4f390796117ec2396fafed9587558e9ba839b7a46a"}
 
 
 def _peaks():
