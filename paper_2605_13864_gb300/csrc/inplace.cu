@@ -215,13 +215,17 @@ InplaceConfig make_inplace()
 
 const InplaceConfig &inplace_config(size_t esize)
 {
-    // Measured on 16384^2 (CUDA events, fraction of the copy peak): fp32 64x64
-    // pairs in a 4-stage ring at one CTA per SM, 0.910 (1 stage at 3 CTAs per
-    // SM 0.882, 2 stages 0.835, 3 stages 0.896, 5 stages 0.908, 2 output
-    // buffers 0.796-0.797); 16-bit 128x128 pairs in a 2-stage ring, 0.858
-    // (64x64 pairs: 1 stage 0.801, 2 output buffers 0.849, 2 stages 0.758;
-    // 128x128 with 1 stage 0.729).
-    static const InplaceConfig c4 = make_inplace<4, 64, 4, 1>();
+    // Measured with CUDA events (fraction of the copy peak; variants compared
+    // only within one run on one GPU).  fp32: 64x64 pairs, one stage and one
+    // output buffer (64 KiB) at three CTAs per SM, 0.919-0.934 on 16384^2,
+    // against 0.914-0.917 for a 4-stage ring at one CTA per SM and 0.835 for
+    // 2 stages; it also wins at 4096^2-12288^2 (e.g. 8192^2 0.870 against
+    // 0.840, L2 flushed).  16-bit: 128x128 pairs in a 2-stage ring at one CTA
+    // per SM, 0.836-0.886 on 16384^2 against 0.80-0.85 for 64x64 pairs in one
+    // stage, and 0.91-0.99 against 0.84-0.91 at 6144^2-8192^2 (64x64 pairs
+    // with 2 output buffers 0.849, 2 stages 0.758; 128x128 in one stage
+    // 0.729).
+    static const InplaceConfig c4 = make_inplace<4, 64, 1, 1>();
     static const InplaceConfig c2 = make_inplace<2, 128, 2, 1>();
     return esize == 4 ? c4 : c2;
 }
