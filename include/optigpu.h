@@ -205,10 +205,11 @@ optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets,
  * parallel prefix sum as future work, Sec. 9).
  *   int32 input    -> dst holds int64 values (exact).
  *   float input    -> dst holds float32 values (fp32, bf16 and fp16 input):
- *                     FP32 inside each 4096-element sub-block, FP64 carries
- *                     between sub-blocks and chunks; within 1e-6 of the sum
+ *                     FP32 inside each chunk (4096 elements; 8192 for 16-bit
+ *                     input; the three-launch form: 4096-element sub-blocks),
+ *                     FP64 carries between chunks; within 1e-6 of the sum
  *                     of |x| over the prefix.
- * Default: one pass over 4096-element chunks claimed in order.  Block (k, m)
+ * Default: one pass over chunks claimed in order.  Block (k, m)
  * is the sum of the totals of chunks [m 32^k, (m+1) 32^k), formed by a fixed
  * butterfly over its 32 children; the carry of chunk c adds, level by level
  * from the top, the complete blocks before c inside its parent group (the

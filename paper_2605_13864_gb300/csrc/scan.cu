@@ -2,10 +2,11 @@
 // (the thesis names parallel prefix sum as future work, Sec. 9; the running
 // sum of Listing 2.1's loop, keeping every intermediate value).
 //
-// Default: one pass (scan_deferred_kernel below): 4096-element chunks claimed
-// in order, TMA-staged, each carried by a sum of radix-32 blocks of earlier
-// chunk totals whose expression depends on the chunk index alone, so results
-// are bit-identical from run to run and no chunk waits on another's carry.
+// Default: one pass (scan_deferred_kernel below): 4096-element chunks (8192
+// for 16-bit input) claimed in order, TMA-staged, each carried by a sum of
+// radix-32 blocks of earlier chunk totals whose expression depends on the
+// chunk index alone, so results are bit-identical from run to run and no
+// chunk waits on another's carry.
 // Each carry is fetched one chunk after the scan that publishes its own
 // chunk and used one chunk later still; scan_onepass_kernel, configuration
 // 2, is the same pass reading each carry at once.
@@ -241,7 +242,7 @@ scan_chunks_kernel(const void *__restrict__ src, void *__restrict__ dst, int64_t
 // ----------------------------------------------------- single pass
 
 // Carries of the single pass, fixed by the chunk index alone.  Chunk c
-// (4096 elements) publishes its total a_c = B(0, c).  Block (k, m) is the
+// (4096 elements, 8192 for 16-bit input) publishes its total a_c = B(0, c).  Block (k, m) is the
 // aligned run of chunks [m 32^k, (m+1) 32^k); its sum is defined by a fixed
 // tree over its 32 children,
 //     B(k+1, m) = tree( B(k, 32m), ..., B(k, 32m + 31) )
@@ -349,22 +350,27 @@ struct OnePass {
     using Out = typename T::Out;
     static constexpr int kInBytes = (DT == OPTIGPU_BFLOAT16 || DT == OPTIGPU_FLOAT16) ? 2 : 4;
     static constexpr int kOutBytes = int(sizeof(Out));
-    // Elements per thread and per chunk.  (8192-element chunks for fp32, at
-    // two CTAs per SM, took 0.92 ms on 2^28 elements against 0.56 ms: the
-    // rate follows the number of resident CTAs, not the bytes per CTA.)
-    static constexpr int kPer = kPerThread;
-    static constexpr int kChunk = kScanThreads * kPer; // 4096
-    static constexpr int kWords = kPer * kInBytes / 4;  // raw 32-bit words per thread
-    static constexpr int kInStage = kChunk * kInBytes;   // 16 KiB or 8 KiB
+    // Elements per thread and per chunk.  The rate follows the chunks an SM
+    // has in flight more than the bytes: every chunk pays the same claim,
+    // publication and carry round trips.  16-bit input uses 8192-element
+    // chunks (16 KiB in, like fp32's 4096) at two CTAs per SM: 2^28 bf16 ->
+    // fp32 in 0.326 ms against 0.406 ms with 4096-element chunks at three
+    // (four CTAs per SM at 4096 gained nothing).  fp32 keeps 4096: 6144-
+    // element chunks at two CTAs per SM took 0.541 ms against 0.459 ms, and
+    // 8192 at two 0.92 ms against 0.56 ms (an earlier kernel).
+    static constexpr int kPer = kInBytes == 2 ? 2 * kPerThread : kPerThread;
+    static constexpr int kChunk = kScanThreads * kPer; // 4096, or 8192 for 16-bit input
+    static constexpr int kWords = kPer * kInBytes / 4;  // raw 32-bit words per thread (16)
+    static constexpr int kInStage = kChunk * kInBytes;   // 16 KiB
     static constexpr int kOutStage = kChunk * kOutBytes; // 16 KiB or 32 KiB
     static constexpr int kSmem = 2 * kInStage + kOutStage + 1024;
     static constexpr int kInRow = 128 / kInBytes;  // elements per 128-byte row
     static constexpr int kOutRow = 128 / kOutBytes;
-    static constexpr int kMinBlocks = 3; // CTAs per SM the register budget is sized for
+    static constexpr int kMinBlocks = kInBytes == 2 ? 2 : 3; // CTAs per SM the register budget is sized for
     // Deferred-carry form: a three-stage input ring; int32 (8-byte outputs)
-    // fits two CTAs per SM, the float types three.
+    // and 16-bit input (32 KiB out stages) fit two CTAs per SM, fp32 three.
     static constexpr int kSmemDeferred = 3 * kInStage + kOutStage + 1024;
-    static constexpr int kMinBlocksDeferred = kOutBytes == 8 ? 2 : 3;
+    static constexpr int kMinBlocksDeferred = (kOutBytes == 8 || kInBytes == 2) ? 2 : 3;
 };
 
 // Element bits (the low 16 bits for 2-byte types) -> in-chunk accumulator.

@@ -89,3 +89,15 @@ def test_noalloc_leaves_device_memory_untouched():
     assert free_after == free_before
     ref = oracle.reduce_reference(a)
     assert abs(out.item() - ref["f64"]) <= 1e-6 * ref["abs"]
+
+
+def test_noalloc_at_its_exact_limit():
+    # 2^29 ones: the largest n the fixed array serves; every partial is exact.
+    L = N.lib()
+    d = torch.ones(LIMIT, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    want = _sum(L.optigpu_reduce_sum_ex, d, "float32", 0, stream)
+    got = _sum(L.optigpu_reduce_sum_noalloc, d, "float32", 0, stream)
+    assert got == want == float(LIMIT)
+    del d
+    torch.cuda.empty_cache()
