@@ -970,8 +970,523 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
         atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
 }
 
+// ----------------------------------------------------- windowed single pass
+
+// Carries fixed by the slice index through 32 interleaved running sums.
+// Slice s (kSubs sub-chunks of 4096 elements) publishes its total T_s.  For
+// each lane l < 32 let
+//     A_l(s) = sum of T_j over j < s with j = l (mod 32), added left to right,
+// and let the exclusive carry of slice s be the lane-0 result of a 5-step
+// XOR butterfly over A_0(s) .. A_31(s).  Every CTA extends the 32 running
+// sums itself (lane l adds the new T_j of its residue class in increasing j)
+// from the published totals, so no CTA waits on another's carry, only on
+// totals; and every term and addition order is fixed by s alone (not by the
+// grid or the timing), so results are bit-identical from run to run.  Sums
+// are int64 for int32 input and FP32 hi + lo pairs (TwoSum) for float input.
+// Inside a slice, sub-chunk q adds the totals of sub-chunks 0 .. q-1 (left
+// to right) to the carry.
+constexpr int kWinWarps = kScanThreads / 32;
+constexpr int kWinMaxCtas = kWinWarps * 32; // 256 CTAs at most: one copy brings in the G new totals
+constexpr int kWinSlotCap = kWinMaxCtas;
+
+// Float carries of the windowed form are FP32 pairs hi + lo (about 44
+// significant bits), added with Knuth's TwoSum and a final fast two-sum:
+// FP64 runs at a small fraction of the FP32 rate on this part, and the
+// carry path is serial.  A non-finite sum passes through hi alone (lo = 0),
+// so infinities and NaN propagate as in a plain running sum.
+struct F2 {
+    float hi, lo;
+    F2() = default;
+    __device__ explicit F2(float h, float l = 0.0f) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float h = s + e;
+    const float l = e - (h - s);
+    // Selects, not branches: the carry warp keeps several sums in flight.
+    const float hi = isfinite(s) ? h : s;
+    return F2(hi, isfinite(hi) ? l : 0.0f);
+}
+__device__ __forceinline__ long long win_add(long long a, long long b) { return a + b; }
+__device__ __forceinline__ F2 win_add(F2 a, F2 b) { return f2_add(a, b); }
+__device__ __forceinline__ long long win_shfl_xor(long long x, int d) { return __shfl_xor_sync(0xffffffffu, x, d); }
+__device__ __forceinline__ F2 win_shfl_xor(F2 x, int d)
+{
+    return F2(__shfl_xor_sync(0xffffffffu, x.hi, d), __shfl_xor_sync(0xffffffffu, x.lo, d));
+}
+__device__ __forceinline__ long long win_of(long long v) { return v; }
+__device__ __forceinline__ F2 win_of(float v) { return F2(v); }
+__device__ __forceinline__ long long win_split(long long c) { return c; }
+__device__ __forceinline__ SplitCarry win_split(F2 c) { return SplitCarry{c.hi, c.lo}; }
+
+template <int DT>
+struct WinPass {
+    using T = ScanTraits<DT>;
+    using Out = typename T::Out;
+    static constexpr int kInBytes = (DT == OPTIGPU_BFLOAT16 || DT == OPTIGPU_FLOAT16) ? 2 : 4;
+    static constexpr int kOutBytes = int(sizeof(Out));
+    static constexpr int kPer = kPerThread;                 // 16 consecutive elements per thread
+    static constexpr int kSubN = kScanThreads * kPer;       // 4096 elements per sub-chunk
+    static constexpr int kWords = kPer * kInBytes / 4;      // raw 32-bit words per thread (16 or 8)
+    static constexpr int kInSub = kSubN * kInBytes;         // 16 or 8 KiB
+    static constexpr int kOutSub = kSubN * kOutBytes;       // 16 or 32 KiB
+    // Sub-chunks per slice: 32 KiB of fp32 in, 24 KiB of 16-bit input (48
+    // KiB out), 16 KiB of int32 (32 KiB of int64 out).
+    static constexpr int kSubs = kOutBytes == 8 ? 1 : (kInBytes == 2 ? 3 : 2);
+    static constexpr int kSlice = kSubs * kSubN;
+    static constexpr int kInStage = kSubs * kInSub, kOutStage = kSubs * kOutSub;
+    // Input stages: slice j being scanned, j-1 .. j-3 waiting for or taking
+    // their carries, j+1 and j+2 loading.
+    static constexpr int kRing = 6;
+    // fp32 is finished in place in its input stage (the same layout in and
+    // out); wider outputs take an out stage.
+    static constexpr bool kInPlace = kInBytes == kOutBytes;
+    static constexpr int kSmem = kRing * kInStage + (kInPlace ? 0 : kOutStage) + 1024;
+    static constexpr int kInRow = 128 / kInBytes, kOutRow = 128 / kOutBytes;
+    // Slice totals, window sums and carries: int64 for int32 input, FP32
+    // pairs for float input.
+    using Carry = typename std::conditional<DT == OPTIGPU_INT32, long long, F2>::type;
+};
+
+// Every sub-chunk of a slice is scanned by its own group of kScanThreads
+// threads (eight warps); `tid` is the thread's index inside its group.
+
+// Sub-chunk staged from plain loads (the ragged last slice, or a source that
+// is not 16-byte aligned) in the swizzled layout of a TMA load; elements past
+// n are zero.
+template <int DT>
+__device__ __forceinline__ void win_stage_plain(unsigned char *sub_ptr, const void *src, int64_t n, int64_t base,
+                                                int tid)
+{
+    using P = WinPass<DT>;
+#pragma unroll 4
+    for (int k = 0; k < P::kPer; ++k) {
+        const int e = tid + k * kScanThreads;
+        const int64_t i = base + e;
+        const uint32_t off = swz128(uint32_t(e * P::kInBytes));
+        if constexpr (P::kInBytes == 4)
+            *reinterpret_cast<uint32_t *>(sub_ptr + off) = i < n ? static_cast<const uint32_t *>(src)[i] : 0u;
+        else
+            *reinterpret_cast<uint16_t *>(sub_ptr + off) = i < n ? static_cast<const uint16_t *>(src)[i] : uint16_t(0);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void win_load_raw(uint32_t sub_addr, uint32_t (&raw)[WinPass<DT>::kWords], int tid)
+{
+    using P = WinPass<DT>;
+    const uint32_t region = uint32_t(tid) * P::kPer * P::kInBytes;
+#pragma unroll
+    for (int q = 0; q < P::kWords / 4; ++q) {
+        const uint4 w = ptx::lds_v4(sub_addr + swz128(region + 16u * q));
+        raw[4 * q] = w.x;
+        raw[4 * q + 1] = w.y;
+        raw[4 * q + 2] = w.z;
+        raw[4 * q + 3] = w.w;
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void win_unpack(const uint32_t (&raw)[WinPass<DT>::kWords],
+                                           typename ScanTraits<DT>::Acc (&v)[WinPass<DT>::kPer])
+{
+#pragma unroll
+    for (int w = 0; w < WinPass<DT>::kWords; ++w) {
+        if constexpr (WinPass<DT>::kInBytes == 4) {
+            v[w] = acc_of_bits<DT>(raw[w]);
+        } else {
+            v[2 * w] = acc_of_bits<DT>(raw[w] & 0xffffu);
+            v[2 * w + 1] = acc_of_bits<DT>(raw[w] >> 16);
+        }
+    }
+}
+
+// Exclusive scan of one value per thread over a group of kScanThreads (the
+// same fixed order as block_exclusive_scan: Kogge-Stone inside each warp,
+// then warp 0 of the group scans the 8 warp totals), with two syncs of the
+// group's named barrier `bar`.  warp_tot must not be reused before a later
+// barrier of the group.
+template <typename T>
+__device__ __forceinline__ T group_exclusive_scan(T v, T *warp_tot, uint32_t bar, int tid, T *total)
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    T incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T up = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d)
+            incl += up;
+    }
+    if (lane == 31)
+        warp_tot[warp] = incl;
+    ptx::named_bar_sync(bar, kScanThreads);
+    if (warp == 0) {
+        T w = lane < kWinWarps ? warp_tot[lane] : T(0);
+#pragma unroll
+        for (int d = 1; d < kWinWarps; d <<= 1) {
+            const T up = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d)
+                w += up;
+        }
+        if (lane < kWinWarps)
+            warp_tot[lane] = w; // inclusive prefix of the warp totals
+    }
+    ptx::named_bar_sync(bar, kScanThreads);
+    const T bw = warp > 0 ? warp_tot[warp - 1] : T(0);
+    *total = warp_tot[kWinWarps - 1];
+    // The left neighbour's inclusive value (incl - v would round, and turn an
+    // infinite own value into NaN).
+    const T left = __shfl_up_sync(0xffffffffu, incl, 1);
+    return lane > 0 ? bw + left : bw;
+}
+
+// The outputs of a sub-chunk into its swizzled out buffer: the thread's run
+// again, plus its group prefix, plus the carry.
+template <int DT>
+__device__ __forceinline__ void win_finish(const uint32_t (&raw)[WinPass<DT>::kWords],
+                                           typename ScanTraits<DT>::Acc before, typename ScanTraits<DT>::Split sc,
+                                           uint32_t out_addr, int tid)
+{
+    using P = WinPass<DT>;
+    using T = ScanTraits<DT>;
+    typename T::Acc v[P::kPer];
+    win_unpack<DT>(raw, v);
+#pragma unroll
+    for (int j = 1; j < P::kPer; ++j)
+        v[j] += v[j - 1];
+    const uint32_t oregion = uint32_t(tid) * P::kPer * P::kOutBytes;
+    if constexpr (P::kOutBytes == 4) {
+#pragma unroll
+        for (int q = 0; q < P::kPer / 4; ++q) {
+            uint4 w;
+            w.x = __float_as_uint(T::finish(sc, before + v[4 * q]));
+            w.y = __float_as_uint(T::finish(sc, before + v[4 * q + 1]));
+            w.z = __float_as_uint(T::finish(sc, before + v[4 * q + 2]));
+            w.w = __float_as_uint(T::finish(sc, before + v[4 * q + 3]));
+            ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < P::kPer / 2; ++q) {
+            const unsigned long long a = static_cast<unsigned long long>(T::finish(sc, before + v[2 * q]));
+            const unsigned long long b2 = static_cast<unsigned long long>(T::finish(sc, before + v[2 * q + 1]));
+            ptx::sts_v4(out_addr + swz128(oregion + 16u * q),
+                        make_uint4(uint32_t(a), uint32_t(a >> 32), uint32_t(b2), uint32_t(b2 >> 32)));
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void win_store_plain(void *dst, int64_t n, int64_t base, const unsigned char *out_sub,
+                                                int tid)
+{
+    using P = WinPass<DT>;
+    using Out = typename ScanTraits<DT>::Out;
+    Out *out = static_cast<Out *>(dst);
+#pragma unroll 4
+    for (int k = 0; k < P::kPer; ++k) {
+        const int e = tid + k * kScanThreads;
+        const int64_t i = base + e;
+        if (i < n)
+            out[i] = *reinterpret_cast<const Out *>(out_sub + swz128(uint32_t(e * P::kOutBytes)));
+    }
+}
+
+// Bounded spin until a shared counter reaches `target`; false on timeout or
+// when the CTA aborts.
+__device__ __forceinline__ bool win_wait_count(const unsigned long long *counter, unsigned long long target,
+                                               const volatile int *abort, uint64_t limit_ns)
+{
+    const volatile unsigned long long *c = counter;
+    if (*c >= target)
+        return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    for (uint32_t spin = 1;; ++spin) {
+        if (*c >= target)
+            return true;
+        if (*abort)
+            return false;
+        if ((spin & 63u) == 0u && ptx::globaltimer_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+
+// Windowed single pass.  One CTA per SM (a cooperative launch, so every CTA
+// is resident while others wait for its totals); CTA b takes slices
+// b, b + G, b + 2G, ... in order.  Group g (eight warps) owns sub-chunk g of
+// every slice and runs its own software pipeline over a six-stage ring:
+//   iteration j:  load sub-chunk g of slice j+2 into the buffer that of
+//                 slice j-4 left; wait for slice j; scan it and hand its total
+//                 to the slice (the last group to arrive adds the S totals and
+//                 publishes the slice total); finish slice j-3 with the
+//                 carry the carry warp prepared, and store it (TMA).
+// The last warp, the carry warp, builds the carry of each slice k once this
+// CTA has published slice k+1 (by then the totals of the slices before k
+// are usually published too): one bulk copy of the G totals since the CTA's
+// previous slice, the 32 running sums and their butterfly, and every
+// sub-chunk's carry as an FP32 hi + lo pair (int64 for int32 input), handed
+// over through shared memory.  Slot words are read with the same complement
+// check as the radix form: a slot copied before it was published is read
+// again (bounded).  fp32 is finished in place in its input buffer; wider
+// outputs go through an out stage.
+template <int DT>
+__global__ void __launch_bounds__(WinPass<DT>::kSubs * kScanThreads + 32, 1)
+scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
+                   const void *__restrict__ src, void *__restrict__ dst, int64_t n, int64_t num_slices,
+                   int64_t full_slices, int in_tma, int out_tma, unsigned long long *totals,
+                   uint64_t wait_limit_ns, unsigned *err)
+{
+    using P = WinPass<DT>;
+    using T = ScanTraits<DT>;
+    using Acc = typename T::Acc;
+    using Carry = typename P::Carry;
+    using Split = typename T::Split;
+    constexpr int S = P::kSubs, R = P::kRing, kW = P::kWords;
+    constexpr int kSplitRing = 4;
+    constexpr bool kInPlace = P::kInPlace;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[R][S];
+    __shared__ __align__(8) uint64_t slot_bar;
+    __shared__ __align__(16) unsigned long long s_slot[2 * kWinSlotCap];
+    __shared__ Acc warp_tot[2][S][kWinWarps];
+    __shared__ Acc s_tot[R][S];              // sub-chunk totals of slice j, at j % R
+    __shared__ unsigned s_arrive[R];         // groups done with slice j, at j % R
+    __shared__ Split s_split[kSplitRing][S]; // carry of each sub-chunk of slice k, at k % 4
+    __shared__ unsigned long long s_published; // slices of this CTA published
+    __shared__ unsigned long long s_ready;     // slices whose carries are in s_split
+    __shared__ volatile int s_abort;
+
+    const uint32_t raw_addr = ptx::smem_addr(smem_raw);
+    const uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
+    unsigned char *stage = smem_raw + pad;
+    const uint32_t stage_addr = raw_addr + pad; // in[0..R) | out (unless in place)
+    const uint32_t sbar = ptx::smem_addr(&slot_bar);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int g = warp / kWinWarps, tid = t - g * kScanThreads; // group, thread in group
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    const int64_t K = b < num_slices ? (num_slices - 1 - b) / G + 1 : 0; // slices of this CTA
+    auto tma_slice = [&](int64_t k) { return in_tma && b + k * G < full_slices; };
+
+    if (t == 0) {
+        for (int r = 0; r < R; ++r) {
+            for (int q = 0; q < S; ++q)
+                ptx::mbar_init(ptx::smem_addr(&full_bar[r][q]), 1);
+            s_arrive[r] = 0;
+        }
+        ptx::mbar_init(sbar, 1);
+        ptx::fence_mbar_init();
+        s_published = 0;
+        s_ready = 0;
+        s_abort = 0;
+    }
+    __syncthreads();
+    bool failed = false;
+
+    if (g == S) {
+        // ------------------------------------------------ the carry warp
+        Carry acc = Carry(0); // A_lane(next): the running sum of this lane's residue class
+        int64_t next = 0;     // totals [0, next) are in acc
+        uint32_t slot_phase = 0;
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t s = b + k * G;
+            // Wait until this CTA has published slice k+1 (its own totals
+            // up to there; the other CTAs' earlier slices are mostly out).
+            if (!win_wait_count(&s_published, (unsigned long long)(k + 2 < K ? k + 2 : K), &s_abort,
+                                wait_limit_ns)) {
+                failed = !s_abort;
+                s_abort = 1;
+                break;
+            }
+            __threadfence_block();
+            const int cnt = int(s - next); // the G totals since this CTA's last slice (s itself at first)
+            if (cnt > 0) {
+                if (lane == 0) {
+                    ptx::fence_proxy_async_smem();
+                    ptx::mbar_arrive_expect_tx(sbar, 16u * uint32_t(cnt));
+                    ptx::bulk_load(ptx::smem_addr(&s_slot[0]), totals + 2 * uint64_t(next), 16u * uint32_t(cnt),
+                                   sbar);
+                }
+                if (!ptx::mbar_wait_bounded(sbar, slot_phase, wait_limit_ns)) {
+                    failed = true; // the copy is still owed: give it one more bounded wait
+                    ptx::mbar_wait_bounded(sbar, slot_phase, wait_limit_ns);
+                    s_abort = 1;
+                    break;
+                }
+                slot_phase ^= 1u;
+                // Lane l adds T_j for the j = l (mod 32) in [next, s), in
+                // increasing j.
+                for (int o = int((uint32_t(lane) - uint32_t(next)) & 31u); o < cnt; o += 32) {
+                    Carry x;
+                    if (!decode_block<Carry>(s_slot[2 * o], s_slot[2 * o + 1], x) &&
+                        !wait_block<Carry>(totals + 2 * (uint64_t(next) + uint64_t(o)), x, wait_limit_ns))
+                        failed = true; // copied before it was published: read it again
+                    acc = win_add(acc, x);
+                }
+            }
+            next = s;
+            __syncwarp(); // every lane has read s_slot before the next copy
+            Carry e = acc;
+#pragma unroll
+            for (int d = 16; d; d >>= 1)
+                e = win_add(e, win_shfl_xor(e, d));
+            if (lane == 0) {
+                // Sub-chunk q adds the totals of sub-chunks 0 .. q-1, left
+                // to right.
+                const int r = int(k % R), e4 = int(k % kSplitRing);
+                Carry cq = e;
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    if (q > 0)
+                        cq = win_add(cq, win_of(s_tot[r][q - 1]));
+                    s_split[e4][q] = win_split(cq);
+                }
+                __threadfence_block();
+                atomicMax(&s_ready, (unsigned long long)(k + 1));
+            }
+        }
+    } else {
+        // ------------------------------------------- compute group g
+        const uint32_t gbar = 1u + uint32_t(g); // the group's named barrier
+        const bool leader = tid == 0;
+        auto in_sub = [&](int r) { return uint32_t(r * P::kInStage + g * P::kInSub); };
+        auto issue_load = [&](int64_t k) { // leader
+            const int r = int(k % R);
+            const uint32_t fb = ptx::smem_addr(&full_bar[r][g]);
+            ptx::mbar_arrive_expect_tx(fb, uint32_t(P::kInSub));
+            ptx::tma_load_3d(stage_addr + in_sub(r), &in_map, 0, 0, int32_t((b + k * G) * S + g), fb);
+        };
+        if (leader) {
+            if (in_tma)
+                ptx::prefetch_tensormap(&in_map);
+            if (out_tma)
+                ptx::prefetch_tensormap(&out_map);
+            for (int64_t k = 0; k < 2 && k < K; ++k)
+                if (tma_slice(k))
+                    issue_load(k);
+        }
+        Acc before_p1 = Acc(0), before_p2 = Acc(0), before_p3 = Acc(0);
+        uint32_t phase = 0;   // bit r: parity of the next completion of this group's buffer of in[r]
+        uint32_t pending = 0; // bit r: a load into it is in flight
+        for (int r = 0; r < 2 && r < K; ++r)
+            if (tma_slice(r))
+                pending |= 1u << r;
+        for (int64_t j = 0; j < K + 3; ++j) {
+            if (leader) {
+                // The store issued last iteration has left shared memory, so
+                // the buffer of slice j-4 (and the out buffer) may be refilled.
+                if (out_tma)
+                    ptx::bulk_wait_group_read<0>();
+                if (j + 2 < K && tma_slice(j + 2)) {
+                    ptx::fence_proxy_async_smem();
+                    issue_load(j + 2);
+                }
+            }
+            if (j + 2 < K && tma_slice(j + 2))
+                pending |= 1u << int((j + 2) % R);
+            Acc before_c = Acc(0);
+            if (j < K) {
+                // ---- slice j: wait, scan, hand over the total
+                const int r = int(j % R);
+                const int64_t s = b + j * G;
+                if (tma_slice(j)) {
+                    const bool ok = ptx::mbar_wait_bounded(ptx::smem_addr(&full_bar[r][g]), (phase >> r) & 1u,
+                                                           wait_limit_ns);
+                    if (ptx::named_bar_or(gbar, kScanThreads, !ok)) {
+                        failed = true; // the buffer stays pending: drained below
+                        break;
+                    }
+                    phase ^= 1u << r;
+                    pending &= ~(1u << r);
+                } else {
+                    win_stage_plain<DT>(stage + in_sub(r), src, n, s * P::kSlice + int64_t(g) * P::kSubN, tid);
+                    ptx::named_bar_sync(gbar, kScanThreads);
+                }
+                uint32_t raw[kW];
+                win_load_raw<DT>(stage_addr + in_sub(r), raw, tid);
+                Acc v[P::kPer];
+                win_unpack<DT>(raw, v);
+                Acc run = Acc(0);
+#pragma unroll
+                for (int e = 0; e < P::kPer; ++e)
+                    run += v[e];
+                Acc tot;
+                before_c = group_exclusive_scan<Acc>(run, warp_tot[j & 1][g], gbar, tid, &tot);
+                if (leader) {
+                    s_tot[r][g] = tot;
+                    __threadfence_block();
+                    if (atomicAdd(&s_arrive[r], 1u) == unsigned(S - 1)) {
+                        // The last group of the slice publishes its total.
+                        __threadfence_block();
+                        s_arrive[r] = 0;
+                        Carry ts = win_of(s_tot[r][0]);
+#pragma unroll
+                        for (int q = 1; q < S; ++q)
+                            ts = win_add(ts, win_of(s_tot[r][q]));
+                        publish_block<Carry>(totals + 2 * uint64_t(s), ts);
+                        __threadfence_block();
+                        atomicMax(&s_published, (unsigned long long)(j + 1));
+                    }
+                }
+            }
+
+            // ---- finish slice j-3 and store it
+            if (j >= 3) {
+                const int64_t k3 = j - 3;
+                const int r3 = int(k3 % R);
+                const int64_t s3 = b + k3 * G;
+                if (leader && !win_wait_count(&s_ready, (unsigned long long)(k3 + 1), &s_abort, wait_limit_ns))
+                    failed = true;
+                if (ptx::named_bar_or(gbar, kScanThreads, failed)) {
+                    failed = true;
+                    break;
+                }
+                __threadfence_block();
+                const uint32_t in3 = stage_addr + in_sub(r3);
+                const uint32_t out3 = kInPlace ? in3 : stage_addr + uint32_t(R * P::kInStage + g * P::kOutSub);
+                uint32_t raw[kW];
+                win_load_raw<DT>(in3, raw, tid);
+                win_finish<DT>(raw, before_p3, s_split[k3 % kSplitRing][g], out3, tid);
+                const bool store_tma = out_tma && s3 < full_slices;
+                if (store_tma)
+                    ptx::fence_proxy_async_smem();
+                ptx::named_bar_sync(gbar, kScanThreads);
+                if (store_tma) {
+                    if (leader) {
+                        ptx::tma_store_3d(&out_map, 0, 0, int32_t(s3 * S + g), out3);
+                        ptx::bulk_commit_group();
+                    }
+                } else {
+                    win_store_plain<DT>(dst, n, s3 * P::kSlice + int64_t(g) * P::kSubN,
+                                        stage + (out3 - stage_addr), tid);
+                    ptx::named_bar_sync(gbar, kScanThreads); // read before it is refilled
+                }
+            }
+            before_p3 = before_p2;
+            before_p2 = before_p1;
+            before_p1 = before_c;
+        }
+        if (failed && leader)
+            s_abort = 1;
+        if (leader) {
+            // Nothing may still write this CTA's shared memory when it exits.
+            for (int r = 0; r < R; ++r)
+                if ((pending >> r) & 1u)
+                    ptx::mbar_wait_bounded(ptx::smem_addr(&full_bar[r][g]), (phase >> r) & 1u, wait_limit_ns);
+            if (out_tma)
+                ptx::bulk_wait_group<0>();
+        }
+    }
+    if (failed)
+        atomicOr(err, DEV_ERR_WAIT_TIMEOUT);
+}
+
 // 0: single pass, carries used one chunk later (scan_deferred_kernel);
-// 1: three passes; 2: single pass, carries read at once (scan_onepass_kernel).
+// 1: three passes; 2: single pass, carries read at once (scan_onepass_kernel);
+// 3: windowed single pass (scan_window_kernel).
 std::atomic<int> g_scan_choice{0};
 
 template <int DT>
@@ -1062,9 +1577,79 @@ optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, int fo
 }
 
 template <int DT>
+optigpu_status launch_scan_window(const void *src, void *dst, int64_t n, cudaStream_t stream)
+{
+    using P = WinPass<DT>;
+    DeviceInfo dev;
+    optigpu_status st = current_device(dev);
+    if (st != OPTIGPU_OK)
+        return st;
+    const int64_t slices = (n + P::kSlice - 1) / P::kSlice, full_slices = n / P::kSlice;
+    const int64_t full_chunks = full_slices * P::kSubs;
+    if (full_chunks > int64_t(INT32_MAX))
+        return fail(OPTIGPU_ERR_INVALID_ARG, "scan: too many chunks for the windowed form");
+    // [slice totals, 16 B each], zeroed.
+    const size_t bytes = size_t(16) * size_t(slices) + 256;
+    void *ws = nullptr;
+    if ((st = stream_workspace(stream, bytes, &ws, 3)) != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaMemsetAsync(ws, 0, bytes, stream), "scan: reset slice totals")) != OPTIGPU_OK)
+        return st;
+
+    CUtensorMap in_map{}, out_map{};
+    const int in_tma = full_chunks > 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+    const int out_tma = full_chunks > 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0;
+    if (in_tma &&
+        (st = encode_tensor_map_3d_swizzled(&in_map, const_cast<void *>(src),
+                                            P::kInBytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                                            P::kInRow, P::kSubN / P::kInRow, uint64_t(full_chunks), 128,
+                                            uint64_t(P::kInSub), P::kInRow, P::kSubN / P::kInRow,
+                                            CU_TENSOR_MAP_SWIZZLE_128B)) != OPTIGPU_OK)
+        return st;
+    if (out_tma &&
+        (st = encode_tensor_map_3d_swizzled(&out_map, dst,
+                                            P::kOutBytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                                              : CU_TENSOR_MAP_DATA_TYPE_UINT64,
+                                            P::kOutRow, P::kSubN / P::kOutRow, uint64_t(full_chunks), 128,
+                                            uint64_t(P::kOutSub), P::kOutRow, P::kSubN / P::kOutRow,
+                                            CU_TENSOR_MAP_SWIZZLE_128B)) != OPTIGPU_OK)
+        return st;
+
+    const void *fn = reinterpret_cast<const void *>(&scan_window_kernel<DT>);
+    static std::atomic<bool> attr_set[64];
+    if (dev.device < 0 || dev.device >= 64 || !attr_set[dev.device].load()) {
+        if ((st = check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P::kSmem),
+                             "cudaFuncSetAttribute(scan window)")) != OPTIGPU_OK)
+            return st;
+        if (dev.device >= 0 && dev.device < 64)
+            attr_set[dev.device].store(true);
+    }
+    // CTAs wait for the totals of other CTAs' slices, so all of them must be
+    // resident at once: one per SM, launched cooperatively.
+    const int64_t grid = std::min<int64_t>({slices, int64_t(dev.num_sms), int64_t(kWinMaxCtas)});
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(P::kSubs * kScanThreads + 32); // a group of eight warps per sub-chunk, the carry warp
+    cfg.dynamicSmemBytes = size_t(P::kSmem);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    unsigned long long *totals = static_cast<unsigned long long *>(ws);
+    return check_cuda(cudaLaunchKernelEx(&cfg, scan_window_kernel<DT>, in_map, out_map, src, dst, n, slices,
+                                         full_slices, in_tma, out_tma, totals, wait_limit_ns(), dev.status_word),
+                      "launch scan (windowed single pass)");
+}
+
+template <int DT>
 optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t stream)
 {
     const int choice = g_scan_choice.load();
+    if (choice == 3)
+        return launch_scan_window<DT>(src, dst, n, stream);
     if (choice != 1)
         return launch_scan_onepass<DT>(src, dst, n, choice, stream);
     using T = ScanTraits<DT>;
@@ -1092,12 +1677,13 @@ optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t s
 
 } // namespace
 
-int scan_num_configs() { return 3; }
+int scan_num_configs() { return 4; }
 const char *scan_config_name(int c)
 {
     return c == 0   ? "scan single pass (carries used one chunk later)"
            : c == 1 ? "scan three passes"
            : c == 2 ? "scan single pass (carries read at once)"
+           : c == 3 ? "scan single pass (windowed carries, one CTA per SM)"
                     : nullptr;
 }
 int scan_selected() { return g_scan_choice.load(); }

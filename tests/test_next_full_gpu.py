@@ -86,7 +86,8 @@ def test_segmented_2p28_float32_16384_segments():
             assert api.reduce_sum(d[lo:hi]).item() == got[s], s
 
 
-@pytest.mark.parametrize("form", [0, 2], ids=["single_pass", "single_pass_carries_at_once"])
+@pytest.mark.parametrize("form", [0, 2, 3], ids=["single_pass", "single_pass_carries_at_once",
+                                                 "single_pass_windowed"])
 @pytest.mark.parametrize("dtype", ["int32", "float32"])
 def test_scan_2p28(dtype, form):
     a = workloads.roofline_vector(N28) if dtype == "float32" else workloads.histogram_values(N28, 1 << 20)

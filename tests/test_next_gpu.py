@@ -132,7 +132,8 @@ def _abs_bits(a, dtype):
     return np.abs(a)
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["single_pass", "three_pass", "single_pass_carries_at_once"])
+@pytest.fixture(params=[0, 1, 2, 3], ids=["single_pass", "three_pass", "single_pass_carries_at_once",
+                                         "single_pass_windowed"])
 def scan_config(request):
     prev = api.tune_selected("scan", torch.float32)
     api.tune_select("scan", torch.float32, request.param)
