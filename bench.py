@@ -802,13 +802,17 @@ def measure_next(reps: int = 10):
     out32 = torch.empty(1 << 28, device="cuda")
     out64 = torch.empty(1 << 28, dtype=torch.int64, device="cuda")
     vb = v.to(torch.bfloat16)
-    scan_default = api.tune_selected("scan", torch.float32)
-    for cfg, tag in ((0, ""), (1, "_three_pass"), (2, "_carries_at_once")):
-        api.tune_select("scan", torch.float32, cfg)
+    # Each scan form in turn (selected for both input classes), the default
+    # forms (windowed for float input, radix single pass for int32) first.
+    scan_default = [api.tune_selected("scan", dt) for dt in (torch.int32, torch.float32)]
+    for cfg, tag in ((None, ""), (0, "_radix"), (1, "_three_pass"), (2, "_carries_at_once"), (3, "_windowed")):
+        for dt, d in zip((torch.int32, torch.float32), scan_default):
+            api.tune_select("scan", dt, d if cfg is None else cfg)
         timed("scan_2p28_fp32" + tag, lambda: api.scan(v, out=out32), (1 << 28) * 8)
         timed("scan_2p28_int32_to_int64" + tag, lambda: api.scan(vi, out=out64), (1 << 28) * 12)
         timed("scan_2p28_bf16_to_fp32" + tag, lambda: api.scan(vb, out=out32), (1 << 28) * 6)
-    api.tune_select("scan", torch.float32, scan_default)
+    for dt, d in zip((torch.int32, torch.float32), scan_default):
+        api.tune_select("scan", dt, d)
     del out32, out64, vb
     timed("histogram_2p28_int32_4096bins", lambda: api.histogram(vi, 0, 1, 4096), (1 << 28) * 4)
     del v, vi
@@ -1054,7 +1058,8 @@ def run_case(args):
             plan.run()
         torch.cuda.synchronize()
         plan.close()
-    elif case in ("scan_f32", "scan_i32", "scan3_f32", "scan3_i32", "scan2_f32", "scan2_i32"):
+    elif case in ("scan_f32", "scan_i32", "scan3_f32", "scan3_i32", "scan2_f32", "scan2_i32", "scanw_f32",
+                  "scanw_i32"):
         n = side * side
         if case.endswith("f32"):
             v = torch.randn(n, device="cuda")
@@ -1062,7 +1067,8 @@ def run_case(args):
         else:
             v = torch.randint(0, 4096, (n,), dtype=torch.int32, device="cuda")
             o = torch.empty(n, dtype=torch.int64, device="cuda")
-        api.tune_select("scan", torch.float32, 1 if case.startswith("scan3") else 2 if case.startswith("scan2") else 0)
+        form = 1 if case.startswith("scan3") else 2 if case.startswith("scan2") else 3 if case.startswith("scanw") else 0
+        api.tune_select("scan", torch.float32 if case.endswith("f32") else torch.int32, form)
         for _ in range(args.case_reps):
             api.scan(v, out=o)
     elif case == "histogram":
@@ -1113,7 +1119,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one kernel case and exit (transpose_tma_f32, transpose_tma_bf16, "
                          "transpose_tile32_f32, reduce_f32, reduce_f32_comp, reduce_bf16_comp, batch, batch_transposes, "
-                         "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, histogram, inplace_f32, inplace_bf16, "
+                         "scan_f32, scan_i32, scan3_f32, scan3_i32, scan2_f32, scan2_i32, scanw_f32, scanw_i32, histogram, inplace_f32, inplace_bf16, "
                          "transpose_batched_f32, segmented_f32)")
     ap.add_argument("--side", type=int, default=8192)
     ap.add_argument("--count", type=int, default=1024)

@@ -73,7 +73,7 @@ typedef enum {
     OPTIGPU_OP_TRANSPOSE = 0,
     OPTIGPU_OP_REDUCE = 1,
     OPTIGPU_OP_BATCH = 2, /* autotuner only: the batch kernel's configurations */
-    OPTIGPU_OP_SCAN = 3   /* tuner: form of the inclusive scan (0, 1, 2; see optigpu_scan_inclusive) */
+    OPTIGPU_OP_SCAN = 3   /* tuner: form of the inclusive scan (0 .. 3; see optigpu_scan_inclusive) */
 } optigpu_op;
 
 /* ------------------------------------------------------------------------ */
@@ -205,23 +205,30 @@ optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets,
  * parallel prefix sum as future work, Sec. 9).
  *   int32 input    -> dst holds int64 values (exact).
  *   float input    -> dst holds float32 values (fp32, bf16 and fp16 input):
- *                     FP32 inside each chunk (4096 elements; 8192 for 16-bit
- *                     input; the three-launch form: 4096-element sub-blocks),
- *                     FP64 carries between chunks; within 1e-6 of the sum
- *                     of |x| over the prefix.
- * Default: one pass over chunks claimed in order.  Block (k, m)
- * is the sum of the totals of chunks [m 32^k, (m+1) 32^k), formed by a fixed
- * butterfly over its 32 children; the carry of chunk c adds, level by level
- * from the top, the complete blocks before c inside its parent group (the
- * base-32 digits of c).  The expression is fixed by c, so the result is
- * bit-identical from run to run (device waits bounded; a wait that gives up
- * is reported by optigpu_stream_status).  Tuner configurations
- * (OPTIGPU_OP_SCAN): 0 = the single pass with each carry used one chunk
- * after it is fetched (default), 1 = three launches (chunk sums, carries,
- * chunk scans), 2 = the single pass reading each carry at once; 0 and 2
- * give the same bits.  src and dst must not overlap; n in [0, 2^40].  Uses a
- * per-stream library workspace of about 4 bytes per 1024 elements.  Errors
- * as optigpu_reduce_sum_ex, plus OVERLAP. */
+ *                     FP32 inside each 4096-element chunk (8192 for 16-bit
+ *                     input in forms 0 and 2), carries between chunks in
+ *                     FP64 (forms 0-2) or FP32 hi + lo pairs (form 3);
+ *                     within 1e-6 of the sum of |x| over the prefix.
+ * Every form fixes the expression of each output by its index alone, so the
+ * result is bit-identical from run to run (device waits bounded; a wait that
+ * gives up is reported by optigpu_stream_status).  Tuner configurations
+ * (OPTIGPU_OP_SCAN), kept per input class (int32; the float types together):
+ *   0  one pass over chunks claimed in order; block (k, m) is the sum of the
+ *      totals of chunks [m 32^k, (m+1) 32^k), formed by a fixed butterfly
+ *      over its 32 children, and the carry of chunk c adds, level by level
+ *      from the top, the complete blocks before c inside its parent group
+ *      (the base-32 digits of c); each carry is used one chunk after it is
+ *      fetched.  The default for int32 input.
+ *   1  three launches (chunk sums, carries, chunk scans).
+ *   2  form 0 reading each carry at once (the same bits as 0).
+ *   3  one pass over slices of 2 (fp32), 3 (16-bit) or 1 (int32) chunks,
+ *      slice s taken by CTA s mod G of a cooperative launch of one CTA per
+ *      SM; the carry of slice s is a fixed butterfly over 32 running sums,
+ *      sum l adding the totals of the slices j < s with j = l (mod 32) left
+ *      to right.  The default for float input.
+ * src and dst must not overlap; n in [0, 2^40].  Uses a per-stream library
+ * workspace of about 4 bytes per 1024 elements.  Errors as
+ * optigpu_reduce_sum_ex, plus OVERLAP. */
 optigpu_status optigpu_scan_inclusive(const void *src, void *dst, int64_t n,
                                       optigpu_dtype dtype, optigpu_stream_t stream);
 
@@ -474,8 +481,10 @@ void optigpu_server_destroy(optigpu_server *server);
  * index 0, the default, picks between indices 1 and 2 by the bytes a call
  * moves (optigpu_transpose_config_for tells which).
  * OPTIGPU_OP_BATCH ignores `dtype`; its selection is the default of new
- * plans.  OPTIGPU_OP_SCAN ignores `dtype`: 0 = single pass (carries used
- * one chunk later), 1 = three passes, 2 = single pass (carries read at once). */
+ * plans.  OPTIGPU_OP_SCAN: 0 = single pass (radix-32 carries used one
+ * chunk later), 1 = three passes, 2 = single pass (carries read at once),
+ * 3 = windowed single pass; the choice is kept per input class (INT32; the
+ * float types together). */
 int optigpu_tune_num_configs(optigpu_op op, optigpu_dtype dtype);
 
 /* Static name of configuration `config`, or NULL if out of range. */

@@ -129,8 +129,9 @@ optigpu_status transpose_band_into(const void *band, void *dst, int64_t b, int64
 // Scan configurations: 0 = single pass (ordered look-back), 1 = three passes.
 int scan_num_configs();
 const char *scan_config_name(int config);
-int scan_selected();
-void scan_select(int config);
+// The scan form is kept per input class (int32; the float types together).
+int scan_selected(int dtype);
+void scan_select(int dtype, int config);
 
 // Batch kernel configurations (default of new plans).
 int batch_num_configs();

@@ -1487,7 +1487,12 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
 // 0: single pass, carries used one chunk later (scan_deferred_kernel);
 // 1: three passes; 2: single pass, carries read at once (scan_onepass_kernel);
 // 3: windowed single pass (scan_window_kernel).
-std::atomic<int> g_scan_choice{0};
+// Kept per input class: [0] int32 input, [1] float input.  The defaults are
+// the fastest measured on 2^28 elements: the radix single pass for int32 ->
+// int64 (its 32 KiB of output per 4096 elements leave the windowed form one
+// group per slice) and the windowed pass for float input.
+std::atomic<int> g_scan_choice[2] = {0, 3};
+int scan_class(int dtype) { return dtype == OPTIGPU_INT32 ? 0 : 1; }
 
 template <int DT>
 optigpu_status launch_scan_onepass(const void *src, void *dst, int64_t n, int form, cudaStream_t stream)
@@ -1647,7 +1652,7 @@ optigpu_status launch_scan_window(const void *src, void *dst, int64_t n, cudaStr
 template <int DT>
 optigpu_status launch_scan(const void *src, void *dst, int64_t n, cudaStream_t stream)
 {
-    const int choice = g_scan_choice.load();
+    const int choice = g_scan_choice[scan_class(DT)].load();
     if (choice == 3)
         return launch_scan_window<DT>(src, dst, n, stream);
     if (choice != 1)
@@ -1686,8 +1691,8 @@ const char *scan_config_name(int c)
            : c == 3 ? "scan single pass (windowed carries, one CTA per SM)"
                     : nullptr;
 }
-int scan_selected() { return g_scan_choice.load(); }
-void scan_select(int c) { g_scan_choice.store(c); }
+int scan_selected(int dtype) { return g_scan_choice[scan_class(dtype)].load(); }
+void scan_select(int dtype, int c) { g_scan_choice[scan_class(dtype)].store(c); }
 
 } // namespace optigpu
 

@@ -131,7 +131,7 @@ optigpu_status optigpu_tune_select(optigpu_op op, optigpu_dtype dtype, int confi
     if (op == OPTIGPU_OP_BATCH)
         batch_select(config);
     else if (op == OPTIGPU_OP_SCAN)
-        scan_select(config);
+        scan_select(int(dtype), config);
     else if (op == OPTIGPU_OP_TRANSPOSE)
         transpose_select(esize_of(dtype), config);
     else
@@ -146,7 +146,7 @@ int optigpu_tune_selected(optigpu_op op, optigpu_dtype dtype)
     if (op == OPTIGPU_OP_BATCH)
         return batch_selected();
     if (op == OPTIGPU_OP_SCAN)
-        return scan_selected();
+        return scan_selected(int(dtype));
     return op == OPTIGPU_OP_TRANSPOSE ? transpose_selected(esize_of(dtype)) : reduce_selected();
 }
 
@@ -213,7 +213,7 @@ optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows
                 continue;
             st = time_median([&] { return transpose_launch_config(a.p, b.p, rows, cols, es, c, s); }, reps, s, ms);
         } else if (op == OPTIGPU_OP_SCAN) {
-            scan_select(c);
+            scan_select(int(dtype), c);
             st = time_median([&] { return optigpu_scan_inclusive(a.p, b.p, n_elems, dtype, s); }, reps, s, ms);
         } else {
             reduce_select(c);
@@ -223,7 +223,7 @@ optigpu_status optigpu_autotune(optigpu_op op, optigpu_dtype dtype, int64_t rows
             if (op == OPTIGPU_OP_REDUCE)
                 reduce_select(prev);
             if (op == OPTIGPU_OP_SCAN)
-                scan_select(prev);
+                scan_select(int(dtype), prev);
             return st;
         }
         if (best < 0 || ms < best_t) {
@@ -255,7 +255,8 @@ optigpu_status optigpu_tune_save(const char *path)
     }
     f << "reduce " << reduce_config_name(reduce_selected()) << "\n";
     f << "batch " << batch_config_name(batch_selected()) << "\n";
-    f << "scan " << scan_config_name(scan_selected()) << "\n";
+    f << "scan int32 " << scan_config_name(scan_selected(OPTIGPU_INT32)) << "\n";
+    f << "scan float " << scan_config_name(scan_selected(OPTIGPU_FLOAT32)) << "\n";
     f << "param transpose.group_rows " << transpose_group_rows() << "\n";
     return f ? OPTIGPU_OK : fail(OPTIGPU_ERR_INVALID_ARG, "tune_save: write failed");
 }
@@ -302,11 +303,24 @@ optigpu_status optigpu_tune_load(const char *path)
                     ++applied;
                 }
         } else if (kind == "scan") {
-            std::string name;
-            std::getline(in >> std::ws, name);
+            // "scan int32 <name>" or "scan float <name>"; a line without the
+            // class names the form of both.
+            std::string rest;
+            std::getline(in >> std::ws, rest);
+            int cls = -1;
+            if (rest.rfind("int32 ", 0) == 0) {
+                cls = OPTIGPU_INT32;
+                rest = rest.substr(6);
+            } else if (rest.rfind("float ", 0) == 0) {
+                cls = OPTIGPU_FLOAT32;
+                rest = rest.substr(6);
+            }
             for (int c = 0; c < scan_num_configs(); ++c)
-                if (name == scan_config_name(c)) {
-                    scan_select(c);
+                if (rest == scan_config_name(c)) {
+                    if (cls != OPTIGPU_FLOAT32)
+                        scan_select(OPTIGPU_INT32, c);
+                    if (cls != OPTIGPU_INT32)
+                        scan_select(OPTIGPU_FLOAT32, c);
                     ++applied;
                 }
         } else if (kind == "param") {

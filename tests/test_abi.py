@@ -181,16 +181,30 @@ def test_tune_cache_round_trip(lib, tmp_path):
 
 def test_tune_cache_keeps_the_scan_form(lib, tmp_path):
     path = str(tmp_path / "tune_scan.txt").encode()
-    assert lib.optigpu_tune_selected(N.OP_SCAN, 0) == 0          # single pass by default
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 1) == N.OK
+    I, F, B = N.INT32, N.FLOAT32, N.BFLOAT16
+    assert lib.optigpu_tune_selected(N.OP_SCAN, I) == 0          # radix single pass for int32
+    assert lib.optigpu_tune_selected(N.OP_SCAN, F) == 3          # windowed single pass for floats
+    assert lib.optigpu_tune_selected(N.OP_SCAN, B) == 3          # one choice for every float type
+    assert lib.optigpu_tune_select(N.OP_SCAN, I, 1) == N.OK
+    assert lib.optigpu_tune_select(N.OP_SCAN, F, 2) == N.OK
+    assert lib.optigpu_tune_selected(N.OP_SCAN, B) == 2
     assert lib.optigpu_tune_save(path) == N.OK
-    assert b"scan " in open(path, "rb").read()
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
+    text = open(path, "rb").read()
+    assert b"scan int32 " in text and b"scan float " in text
+    assert lib.optigpu_tune_select(N.OP_SCAN, I, 0) == N.OK
+    assert lib.optigpu_tune_select(N.OP_SCAN, F, 3) == N.OK
     assert lib.optigpu_tune_load(path) == N.OK
-    assert lib.optigpu_tune_selected(N.OP_SCAN, 0) == 1
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 2) == N.OK
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, lib.optigpu_tune_num_configs(N.OP_SCAN, 0)) == N.ERR_INVALID_ARG
-    assert lib.optigpu_tune_select(N.OP_SCAN, 0, 0) == N.OK
+    assert lib.optigpu_tune_selected(N.OP_SCAN, I) == 1
+    assert lib.optigpu_tune_selected(N.OP_SCAN, F) == 2
+    # A line without the input class sets both classes.
+    name = lib.optigpu_tune_config_name(N.OP_SCAN, F, 3)
+    with open(path, "wb") as fh:
+        fh.write(b"scan " + name + b"\n")
+    assert lib.optigpu_tune_load(path) == N.OK
+    assert lib.optigpu_tune_selected(N.OP_SCAN, I) == 3 and lib.optigpu_tune_selected(N.OP_SCAN, F) == 3
+    assert lib.optigpu_tune_select(N.OP_SCAN, F, lib.optigpu_tune_num_configs(N.OP_SCAN, F)) == N.ERR_INVALID_ARG
+    assert lib.optigpu_tune_select(N.OP_SCAN, I, 0) == N.OK
+    assert lib.optigpu_tune_select(N.OP_SCAN, F, 3) == N.OK
 
 
 def test_server_validation_is_host_side(lib):

@@ -92,12 +92,13 @@ def test_segmented_2p28_float32_16384_segments():
 def test_scan_2p28(dtype, form):
     a = workloads.roofline_vector(N28) if dtype == "float32" else workloads.histogram_values(N28, 1 << 20)
     d = to_device(a, dtype)
-    prev = api.tune_selected("scan", torch.float32)
-    api.tune_select("scan", torch.float32, form)
+    tdt = torch.int32 if dtype == "int32" else torch.float32
+    prev = api.tune_selected("scan", tdt)
+    api.tune_select("scan", tdt, form)
     try:
         got = api.scan(d)
     finally:
-        api.tune_select("scan", torch.float32, prev)
+        api.tune_select("scan", tdt, prev)
     torch.cuda.synchronize()
     api.stream_status()
     del d
@@ -112,9 +113,9 @@ def test_scan_2p28(dtype, form):
 
 
 def test_scan_2p28_repeatable():
-    # The default single pass under full HBM load: carries are fetched by
-    # asynchronous copies and used one chunk later, and still every run gives
-    # the same bits.
+    # The default pass for fp32 (windowed) under full HBM load: slice totals
+    # are fetched by asynchronous copies while other CTAs are still
+    # publishing, and still every run gives the same bits.
     d = to_device(workloads.roofline_vector(N28), "float32")
     out = torch.empty(N28, dtype=torch.float32, device="cuda")
     api.scan(d, out=out)

@@ -135,10 +135,13 @@ def _abs_bits(a, dtype):
 @pytest.fixture(params=[0, 1, 2, 3], ids=["single_pass", "three_pass", "single_pass_carries_at_once",
                                          "single_pass_windowed"])
 def scan_config(request):
-    prev = api.tune_selected("scan", torch.float32)
-    api.tune_select("scan", torch.float32, request.param)
+    # The form is kept per input class: select it for int32 and for floats.
+    prev = [api.tune_selected("scan", dt) for dt in (torch.int32, torch.float32)]
+    for dt in (torch.int32, torch.float32):
+        api.tune_select("scan", dt, request.param)
     yield request.param
-    api.tune_select("scan", torch.float32, prev)
+    for dt, p in zip((torch.int32, torch.float32), prev):
+        api.tune_select("scan", dt, p)
 
 
 @pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16", "float16"])
@@ -222,7 +225,14 @@ def test_scan_autotune_selects_a_form():
     got = api.scan(to_device(a, "float32")).cpu().numpy().astype(np.float64)
     scale = oracle.scan(np.abs(a), "float32")
     assert (np.abs(got - oracle.scan(a, "float32")) <= 1e-6 * scale + 1e-30).all()
-    api.tune_select("scan", torch.float32, 0)
+    api.tune_select("scan", torch.float32, 3)
+
+
+def test_scan_default_forms_per_input_class():
+    # The windowed pass for float input, the radix pass for int32 input.
+    assert api.tune_selected("scan", torch.float32) == 3
+    assert api.tune_selected("scan", torch.bfloat16) == 3
+    assert api.tune_selected("scan", torch.int32) == 0
 
 
 @pytest.mark.parametrize("dtype,n", [("float32", (1 << 24) + 77), ("int32", (1 << 23) + 5),
@@ -233,14 +243,15 @@ def test_scan_single_pass_forms_give_the_same_bits(dtype, n):
     # read differs.
     a = workloads.vector(n, dtype, seed=n + 31)
     d = to_device(a, dtype)
-    prev = api.tune_selected("scan", torch.float32)
+    tdt = torch.int32 if dtype == "int32" else torch.float32
+    prev = api.tune_selected("scan", tdt)
     try:
-        api.tune_select("scan", torch.float32, 0)
+        api.tune_select("scan", tdt, 0)
         first = api.scan(d).cpu().numpy()
-        api.tune_select("scan", torch.float32, 2)
+        api.tune_select("scan", tdt, 2)
         second = api.scan(d).cpu().numpy()
     finally:
-        api.tune_select("scan", torch.float32, prev)
+        api.tune_select("scan", tdt, prev)
     assert first.tobytes() == second.tobytes()
 
 
