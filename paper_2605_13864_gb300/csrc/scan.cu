@@ -986,8 +986,9 @@ scan_deferred_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_co
 // Inside a slice, sub-chunk q adds the totals of sub-chunks 0 .. q-1 (left
 // to right) to the carry.
 constexpr int kWinWarps = kScanThreads / 32;
-constexpr int kWinMaxCtas = kWinWarps * 32; // 256 CTAs at most: one copy brings in the G new totals
-constexpr int kWinSlotCap = kWinMaxCtas;
+constexpr int kWinMaxCtas = kWinWarps * 32; // 256 CTAs at most
+constexpr int kCarryWarps = 2;               // carry warps, taking alternate slices of their CTA
+constexpr int kWinSlotCap = kCarryWarps * kWinMaxCtas; // totals one copy may bring in
 
 // Float carries of the windowed form are FP32 pairs hi + lo (about 44
 // significant bits), added with Knuth's TwoSum and a final fast two-sum:
@@ -1007,7 +1008,7 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b)
     const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
     const float h = s + e;
     const float l = e - (h - s);
-    // Selects, not branches: the carry warp keeps several sums in flight.
+    // Selects, not branches: the carry warps keep several sums in flight.
     const float hi = isfinite(s) ? h : s;
     return F2(hi, isfinite(hi) ? l : 0.0f);
 }
@@ -1223,18 +1224,18 @@ __device__ __forceinline__ bool win_wait_count(const unsigned long long *counter
 //                 slice j-4 left; wait for slice j; scan it and hand its total
 //                 to the slice (the last group to arrive adds the S totals and
 //                 publishes the slice total); finish slice j-3 with the
-//                 carry the carry warp prepared, and store it (TMA).
-// The last warp, the carry warp, builds the carry of each slice k once this
-// CTA has published slice k+1 (by then the totals of the slices before k
-// are usually published too): one bulk copy of the G totals since the CTA's
-// previous slice, the 32 running sums and their butterfly, and every
+//                 carry a carry warp prepared, and store it (TMA).
+// Two carry warps, taking alternate slices, build the carry of each slice k
+// once this CTA has published slice k+1 (by then the totals of the slices
+// before k are usually published too): one bulk copy of the totals since the
+// warp's previous slice, the 32 running sums and their butterfly, and every
 // sub-chunk's carry as an FP32 hi + lo pair (int64 for int32 input), handed
 // over through shared memory.  Slot words are read with the same complement
 // check as the radix form: a slot copied before it was published is read
 // again (bounded).  fp32 is finished in place in its input buffer; wider
 // outputs go through an out stage.
 template <int DT>
-__global__ void __launch_bounds__(WinPass<DT>::kSubs * kScanThreads + 32, 1)
+__global__ void __launch_bounds__(WinPass<DT>::kSubs * kScanThreads + 32 * kCarryWarps, 1)
 scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map,
                    const void *__restrict__ src, void *__restrict__ dst, int64_t n, int64_t num_slices,
                    int64_t full_slices, int in_tma, int out_tma, unsigned long long *totals,
@@ -1250,21 +1251,20 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
     constexpr bool kInPlace = P::kInPlace;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[R][S];
-    __shared__ __align__(8) uint64_t slot_bar;
-    __shared__ __align__(16) unsigned long long s_slot[2 * kWinSlotCap];
+    __shared__ __align__(8) uint64_t slot_bar[kCarryWarps];
+    __shared__ __align__(16) unsigned long long s_slot[kCarryWarps][2 * kWinSlotCap];
     __shared__ Acc warp_tot[2][S][kWinWarps];
     __shared__ Acc s_tot[R][S];              // sub-chunk totals of slice j, at j % R
     __shared__ unsigned s_arrive[R];         // groups done with slice j, at j % R
     __shared__ Split s_split[kSplitRing][S]; // carry of each sub-chunk of slice k, at k % 4
     __shared__ unsigned long long s_published; // slices of this CTA published
-    __shared__ unsigned long long s_ready;     // slices whose carries are in s_split
+    __shared__ unsigned long long s_ready[kCarryWarps]; // carry warp c: its slices up to s_ready[c] - 1 are in s_split
     __shared__ volatile int s_abort;
 
     const uint32_t raw_addr = ptx::smem_addr(smem_raw);
     const uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
     unsigned char *stage = smem_raw + pad;
     const uint32_t stage_addr = raw_addr + pad; // in[0..R) | out (unless in place)
-    const uint32_t sbar = ptx::smem_addr(&slot_bar);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int g = warp / kWinWarps, tid = t - g * kScanThreads; // group, thread in group
     const int64_t G = gridDim.x, b = blockIdx.x;
@@ -1277,21 +1277,28 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
                 ptx::mbar_init(ptx::smem_addr(&full_bar[r][q]), 1);
             s_arrive[r] = 0;
         }
-        ptx::mbar_init(sbar, 1);
+        for (int c = 0; c < kCarryWarps; ++c) {
+            ptx::mbar_init(ptx::smem_addr(&slot_bar[c]), 1);
+            s_ready[c] = 0;
+        }
         ptx::fence_mbar_init();
         s_published = 0;
-        s_ready = 0;
         s_abort = 0;
     }
     __syncthreads();
     bool failed = false;
 
     if (g == S) {
-        // ------------------------------------------------ the carry warp
+        // ------------------------------------------------ a carry warp
+        // Carry warp c takes this CTA's slices k = c (mod kCarryWarps), so
+        // two slices' carries are built at once.
+        const int c = warp - S * kWinWarps;
+        const uint32_t sbar = ptx::smem_addr(&slot_bar[c]);
+        unsigned long long *slots = s_slot[c];
         Carry acc = Carry(0); // A_lane(next): the running sum of this lane's residue class
         int64_t next = 0;     // totals [0, next) are in acc
         uint32_t slot_phase = 0;
-        for (int64_t k = 0; k < K; ++k) {
+        for (int64_t k = c; k < K; k += kCarryWarps) {
             const int64_t s = b + k * G;
             // Wait until this CTA has published slice k+1 (its own totals
             // up to there; the other CTAs' earlier slices are mostly out).
@@ -1302,13 +1309,12 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
                 break;
             }
             __threadfence_block();
-            const int cnt = int(s - next); // the G totals since this CTA's last slice (s itself at first)
+            const int cnt = int(s - next); // the totals since this warp's last slice: at most kWinSlotCap
             if (cnt > 0) {
                 if (lane == 0) {
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive_expect_tx(sbar, 16u * uint32_t(cnt));
-                    ptx::bulk_load(ptx::smem_addr(&s_slot[0]), totals + 2 * uint64_t(next), 16u * uint32_t(cnt),
-                                   sbar);
+                    ptx::bulk_load(ptx::smem_addr(slots), totals + 2 * uint64_t(next), 16u * uint32_t(cnt), sbar);
                 }
                 if (!ptx::mbar_wait_bounded(sbar, slot_phase, wait_limit_ns)) {
                     failed = true; // the copy is still owed: give it one more bounded wait
@@ -1321,7 +1327,7 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
                 // increasing j.
                 for (int o = int((uint32_t(lane) - uint32_t(next)) & 31u); o < cnt; o += 32) {
                     Carry x;
-                    if (!decode_block<Carry>(s_slot[2 * o], s_slot[2 * o + 1], x) &&
+                    if (!decode_block<Carry>(slots[2 * o], slots[2 * o + 1], x) &&
                         !wait_block<Carry>(totals + 2 * (uint64_t(next) + uint64_t(o)), x, wait_limit_ns))
                         failed = true; // copied before it was published: read it again
                     acc = win_add(acc, x);
@@ -1345,7 +1351,7 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
                     s_split[e4][q] = win_split(cq);
                 }
                 __threadfence_block();
-                atomicMax(&s_ready, (unsigned long long)(k + 1));
+                atomicMax(&s_ready[c], (unsigned long long)(k + 1));
             }
         }
     } else {
@@ -1438,7 +1444,8 @@ scan_window_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_cons
                 const int64_t k3 = j - 3;
                 const int r3 = int(k3 % R);
                 const int64_t s3 = b + k3 * G;
-                if (leader && !win_wait_count(&s_ready, (unsigned long long)(k3 + 1), &s_abort, wait_limit_ns))
+                if (leader && !win_wait_count(&s_ready[k3 % kCarryWarps], (unsigned long long)(k3 + 1), &s_abort,
+                                              wait_limit_ns))
                     failed = true;
                 if (ptx::named_bar_or(gbar, kScanThreads, failed)) {
                     failed = true;
@@ -1635,7 +1642,7 @@ optigpu_status launch_scan_window(const void *src, void *dst, int64_t n, cudaStr
     const int64_t grid = std::min<int64_t>({slices, int64_t(dev.num_sms), int64_t(kWinMaxCtas)});
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(P::kSubs * kScanThreads + 32); // a group of eight warps per sub-chunk, the carry warp
+    cfg.blockDim = dim3(P::kSubs * kScanThreads + 32 * kCarryWarps); // a group of eight warps per sub-chunk, the carry warps
     cfg.dynamicSmemBytes = size_t(P::kSmem);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
