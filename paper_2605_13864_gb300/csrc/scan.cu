@@ -1048,7 +1048,7 @@ struct WinPass {
     static constexpr bool kInPlace = kInBytes == kOutBytes;
     static constexpr int kSmem = kRing * kInStage + (kInPlace ? 0 : kOutStage) + 1024;
     static constexpr int kInRow = 128 / kInBytes, kOutRow = 128 / kOutBytes;
-    // Slice totals, window sums and carries: int64 for int32 input, FP32
+    // Slice totals, running sums and carries: int64 for int32 input, FP32
     // pairs for float input.
     using Carry = typename std::conditional<DT == OPTIGPU_INT32, long long, F2>::type;
 };
