@@ -4,8 +4,9 @@ The other parity tests stop at 2^28 elements.  These cover the index
 arithmetic past 2^31 and 2^32 elements with inputs built on the device (tens
 of GB; a GB300 holds 288 GB) and results fixed by their definition, so no
 host copy is needed: a sum of ones is n, an inclusive scan of ones is
-i + 1, a histogram of zeros is n in bin 0, and the transpose of the matrix
-whose entries are their own linear index has dst[c, r] = r * cols + c.
+i + 1 (exactly as int64, or rounded once to fp32), a histogram of zeros is
+n in bin 0, and the transpose of the matrix whose entries are their own
+linear index has dst[c, r] = r * cols + c.
 """
 import numpy as np
 import pytest
@@ -57,6 +58,26 @@ def test_scan_of_ones_past_2p32_elements():
                      torch.arange(N_BIG - 4096, N_BIG, device="cuda")])
     assert torch.equal(out[idx], idx + 1)  # inclusive prefix of ones
     del x, out, idx
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_float_scan_of_ones_past_2p32_elements(dtype):
+    # The windowed pass (the float default) past 2^32 elements: 2^20 chunks,
+    # a ragged last slice.  Every carry is an integer below 2^33, exact in its
+    # FP32 hi + lo pair, and every in-chunk prefix is exact, so each output is
+    # the single rounding of i + 1 to fp32.
+    assert api.tune_selected("scan", dtype) == 3
+    x = torch.ones(N_BIG, dtype=dtype, device="cuda")
+    out = api.scan(x)  # fp32, 17 GB
+    del x
+    torch.cuda.synchronize()
+    api.stream_status()
+    idx = torch.cat([torch.arange(0, 4096, device="cuda"),
+                     torch.randint(0, N_BIG, (1 << 20,), device="cuda", generator=torch.Generator("cuda").manual_seed(3)),
+                     torch.arange(N_BIG - 12288, N_BIG, device="cuda")])
+    assert torch.equal(out[idx], (idx + 1).to(torch.float32))
+    del out, idx
     torch.cuda.empty_cache()
 
 
