@@ -59,6 +59,13 @@ reduce_sum_kernel(const void *__restrict__ src, int64_t n, int vec_ok, void *par
     using Core = ReduceCore<DT, COMP, WAVE ? 4 : 8>;
     __shared__ typename Core::Shared sh;
     __shared__ int s_last;
+    // Launched with programmatic stream serialisation: wait until the
+    // previous kernel on the stream has finished and its writes are visible
+    // (it may be the previous sum, on the same workspace), before touching
+    // memory; then let the next kernel on the stream be launched, so that its
+    // launch overlaps this sum's tail.  Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (int64_t c = blockIdx.x; c < num_chunks; c += gridDim.x) {
         const auto part = Core::chunk_partial(src, n, c, vec_ok != 0, sh);
         if (threadIdx.x == 0)
@@ -171,16 +178,28 @@ optigpu_status persistent_grid(int64_t num_chunks, int64_t *grid, bool *wave)
     return OPTIGPU_OK;
 }
 
+// Programmatic dependent launch: a sum queued right behind another kernel
+// may be launched while that kernel finishes (the kernel waits for it before
+// touching memory), which takes the launch latency off back-to-back sums.
 template <int DT, bool COMP>
-void launch_sum_kernel(bool wave, int64_t grid, cudaStream_t stream, const void *src, int64_t n, int vec_ok,
-                       void *partials, unsigned *counter, void *out, int64_t num_chunks)
+cudaError_t launch_sum_kernel(bool wave, int64_t grid, cudaStream_t stream, const void *src, int64_t n, int vec_ok,
+                              void *partials, unsigned *counter, void *out, int64_t num_chunks)
 {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kReduceThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (wave)
-        reduce_sum_kernel<DT, COMP, true><<<unsigned(grid), kReduceThreads, 0, stream>>>(
-            src, n, vec_ok, partials, counter, out, num_chunks);
-    else
-        reduce_sum_kernel<DT, COMP, false><<<unsigned(grid), kReduceThreads, 0, stream>>>(
-            src, n, vec_ok, partials, counter, out, num_chunks);
+        return cudaLaunchKernelEx(&cfg, reduce_sum_kernel<DT, COMP, true>, src, n, vec_ok, partials, counter, out,
+                                  num_chunks);
+    return cudaLaunchKernelEx(&cfg, reduce_sum_kernel<DT, COMP, false>, src, n, vec_ok, partials, counter, out,
+                              num_chunks);
 }
 
 template <int DT, bool COMP>
@@ -199,8 +218,9 @@ optigpu_status launch(const void *src, int64_t n, void *out, cudaStream_t stream
     unsigned *counter = static_cast<unsigned *>(ws);
     void *partials = static_cast<char *>(ws) + kReduceCounterBytes;
     const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
-    launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out, num_chunks);
-    return check_cuda(cudaGetLastError(), "launch reduce");
+    return check_cuda(launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out,
+                                                  num_chunks),
+                      "launch reduce");
 }
 
 template <int DT, bool COMP>
@@ -429,8 +449,9 @@ optigpu_status launch_noalloc(const void *src, int64_t n, void *out, cudaStream_
                          "reduce_sum_noalloc: clear counter")) != OPTIGPU_OK)
         return st;
     const int vec_ok = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 ? 1 : 0;
-    launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out, num_chunks);
-    return check_cuda(cudaGetLastError(), "launch reduce (noalloc)");
+    return check_cuda(launch_sum_kernel<DT, COMP>(wave, grid, stream, src, n, vec_ok, partials, counter, out,
+                                                  num_chunks),
+                      "launch reduce (noalloc)");
 }
 
 } // namespace
