@@ -176,6 +176,11 @@ int optigpu_transpose_config_for(int64_t rows, int64_t cols, optigpu_dtype dtype
  * not happen during stream capture.  A later, larger sum on the stream gets a
  * new, larger workspace; the old one is retired but stays allocated until
  * optigpu_release_workspaces(), so a CUDA graph captured with it stays valid.
+ * The kernel is launched with programmatic stream serialisation: it may be
+ * launched while the previous kernel on the stream is still running, and
+ * every CTA waits for that kernel to finish (and its writes to be visible)
+ * before touching memory, so stream order is kept; back-to-back sums overlap
+ * a launch with the previous sum's tail.
  * Returns INVALID_ARG, UNSUPPORTED_DTYPE, OOM or CUDA. */
 optigpu_status optigpu_reduce_sum(const void *src, int64_t n,
                                   optigpu_dtype dtype, void *out,
