@@ -54,8 +54,8 @@ METRIC = "transpose/reduce HBM GB/s (% of GB300 peak); batched+served req/s and 
 # DRAM traffic of one transpose launch (16384x16384 fp32, TMA kernel) from an
 # ncu capture; kept only while the kernel's sources are unchanged (sha256 of
 # TRANSPOSE_SOURCES below).
-NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073772800 + 1024100096,
-                         "src_sha256": "b84e73f642bf287d525d0f4f390796117ec2396fafed9587558e9ba839b7a46a"}
+NCU_TRANSPOSE_TRAFFIC = {"bytes": 1073986048 + 1024155392,
+                         "src_sha256": "e28f24a876d589bb3e7f8be43ae0d9aacedf7974bdb3b8a709f1fbf644ad1774"}
 
 
 def _peaks():

@@ -91,7 +91,10 @@ typedef enum {
     /* Persistent kernel: TMA 2-D tile loads into a multi-stage shared-memory
      * ring (mbarrier completion), 16-byte micro-block transposes in
      * registers, TMA 2-D tile stores.  Needs 16-byte aligned src/dst and
-     * rows, cols multiples of 16 / element size. */
+     * rows, cols multiples of 16 / element size.  Launched with
+     * programmatic stream serialisation: it may be launched while the
+     * previous kernel on the stream runs, and waits for it to finish (and
+     * its writes to be visible) before any tile moves. */
     OPTIGPU_TRANSPOSE_TMA = 2
 } optigpu_transpose_kernel;
 

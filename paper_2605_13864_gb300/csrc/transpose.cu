@@ -137,6 +137,14 @@ transpose_tma_kernel(const __grid_constant__ CUtensorMap tm_src,
     const int64_t first = blockIdx.x, stride = gridDim.x;
     const int64_t my_count = first < num_tiles ? (num_tiles - 1 - first) / stride + 1 : 0;
 
+    // Launched with programmatic stream serialisation: wait until the
+    // previous kernel on the stream has finished and its writes are visible
+    // before any tile moves, then let the next kernel be launched (it waits
+    // in turn), so back-to-back calls overlap a launch with this one's tail.
+    // Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     if (t == 0) {
         ptx::prefetch_tensormap(&tm_src);
         ptx::prefetch_tensormap(&tm_dst);
@@ -461,8 +469,17 @@ optigpu_status launch_tma(const void *src, void *dst, int64_t rows, int64_t cols
                     per_mat, int32_t(rows), int32_t(cols)};
     void *args[] = {&ms, &md, &order, const_cast<int64_t *>(&num_tiles), const_cast<uint64_t *>(&limit),
                     &dev.status_word};
-    return check_cuda(cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(unsigned(c.threads)), args, smem, stream),
-                      "launch transpose tma");
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(c.threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return check_cuda(cudaLaunchKernelExC(&cfg, fn, args), "launch transpose tma");
 }
 
 optigpu_status launch_tile32(const void *src, void *dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
