@@ -9,7 +9,8 @@ benchmark times, and compares with the CPU oracle:
   sum of |x|, and sampled segments bit-identical to their single calls;
 - the 2^28-element inclusive scans: every element of int32 -> int64 exact,
   float32 within 1e-6 of the running sum of |x|;
-- the 2^28-value histogram in 4096 bins: exact.
+- the 2^28-value histogram in 4096 bins: exact;
+- two windowed scans on concurrent streams: the same bits as alone.
 """
 import numpy as np
 import pytest
@@ -124,6 +125,34 @@ def test_scan_2p28_repeatable():
         api.scan(d, out=out)
         assert torch.equal(out.view(torch.int32), first)
     api.stream_status()
+
+
+def test_windowed_scans_on_concurrent_streams():
+    # The windowed pass's CTAs wait for one another's slice totals, which is
+    # safe because its launch is cooperative (every CTA resident at once).
+    # Two 2^26 scans issued on two streams with no sync between them, and a
+    # 2^28 sum on a third, give the same bits as the scans run alone, and no
+    # bounded wait gives up.
+    n = 1 << 26
+    xs = [to_device(workloads.vector(n, "float32", seed=90 + k), "float32") for k in range(2)]
+    alone = [api.scan(x) for x in xs]
+    torch.cuda.synchronize()
+    v = to_device(workloads.roofline_vector(N28), "float32")
+    want_sum = api.reduce_sum(v).item()
+    outs = [torch.empty_like(a) for a in alone]
+    s_sum = torch.empty((), dtype=torch.float64, device="cuda")
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        api.scan(xs[0], out=outs[0], stream=streams[0])
+        api.scan(xs[1], out=outs[1], stream=streams[1])
+        api.reduce_sum(v, out=s_sum, stream=streams[2])
+        torch.cuda.synchronize()
+        api.stream_status()
+        for o, a in zip(outs, alone):
+            assert torch.equal(o.view(torch.int32), a.view(torch.int32)), rep
+        assert s_sum.item() == want_sum
+    del xs, alone, outs, v
 
 
 def test_histogram_2p28_4096_bins():
