@@ -197,6 +197,26 @@ def test_scan_unaligned_pointers(dtype, n, scan_config):
         assert (np.abs(g.astype(np.float64) - want) <= 1e-6 * scale + 1e-30).all()
 
 
+@pytest.mark.parametrize("dtype", ["int32", "float32", "bfloat16"])
+@pytest.mark.parametrize("src_off,dst_off", [(0, 1), (1, 0)])
+def test_scan_mixed_alignment(dtype, src_off, dst_off, scan_config):
+    # One pointer on the 16-byte grid and the other off it: TMA loads with
+    # plain stores, and plain loads with TMA stores; the bits equal the
+    # aligned call's (the expression of each output depends on its index
+    # only, not on how the chunk moved).
+    n = 3 * 8192 * 5 + 77
+    a = workloads.vector(n, dtype, seed=n + src_off + 2 * dst_off)
+    aligned = api.scan(to_device(a, dtype))
+    d = to_device(a, dtype, offset_elems=src_off)
+    odt = torch.int64 if dtype == "int32" else torch.float32
+    out = torch.empty(n + dst_off, dtype=odt, device="cuda")[dst_off:]
+    api.scan(d, out=out)
+    torch.cuda.synchronize()
+    api.stream_status()
+    assert torch.equal(out.view(torch.int32) if odt == torch.float32 else out,
+                       aligned.view(torch.int32) if odt == torch.float32 else aligned)
+
+
 @pytest.mark.parametrize("n", [4096 * 5 + 3, 1 << 20])
 def test_scan_infinities_and_nan(n, scan_config):
     # IEEE semantics of the running sum: +inf from the first +inf on, NaN
