@@ -200,10 +200,12 @@ optigpu_status optigpu_reduce_sum_ex(const void *src, int64_t n,
  *   offsets  HOST array of nseg + 1 non-decreasing element offsets (< 2^40).
  *   out      device array of nseg 8-byte results (int64 / double); empty
  *            segments give 0.
- * The offsets go to the device in one asynchronous copy through pinned
- * staging; one small kernel builds the batch tables from them, then all
- * segments run in one launch of the batch kernel (one work item per
- * 16384-element chunk of every segment).  Uses a per-stream library
+ * The offsets are staged in pinned host memory; one small kernel reads them
+ * there (or from one asynchronous upload, where the device cannot address
+ * pinned memory) and builds the batch tables, then all segments run in one
+ * launch of the batch kernel (one work item per 16384-element chunk of every
+ * segment).  The call returns without waiting for the device, except to
+ * reuse a staging buffer of two calls before.  Uses a per-stream library
  * workspace (allocated on first use).  Errors as optigpu_reduce_sum_ex. */
 optigpu_status optigpu_reduce_segmented(const void *src, const int64_t *offsets, int32_t nseg,
                                         optigpu_dtype dtype, void *out, uint32_t flags,

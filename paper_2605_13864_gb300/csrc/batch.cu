@@ -803,50 +803,47 @@ optigpu_status seg_stage_buffer(cudaStream_t s, size_t bytes, void **buf, cudaEv
     return OPTIGPU_OK;
 }
 
-// The tables of a segmented sum in one launch, one thread per segment and
-// per item.  Thread k < nseg writes instance k (segment k; its items, the
-// 16384-element chunks, start at first[k]; an empty segment gets no item and
-// a zero result) and zeroes its completion counter; thread i < items finds
-// its segment, the largest s with first[s] <= i, by binary search over
-// first[]; thread 0 also zeroes the work queue.
+// The tables of a segmented sum in one launch, one warp per segment: lane 0
+// writes instance k (segment k; its items, the 16384-element chunks, start
+// at first[k]; an empty segment gets no item and a zero result) and zeroes
+// its completion counter, and the warp's lanes write k into the item map for
+// every item of the segment; thread 0 also zeroes the work queue.  offsets
+// and first may be host memory mapped for the device (one read of each per
+// segment, all in flight together).
 __global__ void seg_tables_kernel(const char *src, int64_t esize, int dtype, char *out, const int64_t *offsets,
-                                  const int64_t *first, int32_t nseg, int64_t items, BatchInst *insts,
-                                  uint32_t *item_inst, unsigned long long *queue, unsigned *done)
+                                  const int64_t *first, int32_t nseg, BatchInst *insts, uint32_t *item_inst,
+                                  unsigned long long *queue, unsigned *done)
 {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i == 0)
+    const int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k == 0 && lane == 0)
         *queue = 0ull;
-    if (i < nseg) {
-        const int64_t len = offsets[i + 1] - offsets[i];
+    if (k >= nseg)
+        return;
+    const int64_t o0 = offsets[k], o1 = offsets[k + 1], f0 = first[k];
+    const int64_t len = o1 - o0;
+    const int32_t nitems = int32_t((len + kReduceChunk - 1) / kReduceChunk);
+    if (lane == 0) {
         BatchInst b;
-        b.src = src + offsets[i] * esize;
-        b.dst = out + 8 * i;
+        b.src = src + o0 * esize;
+        b.dst = out + 8 * k;
         b.rows = len;
         b.cols = 1;
-        b.first_item = first[i];
-        b.aux = first[i]; // one partial per chunk, in item order
+        b.first_item = f0;
+        b.aux = f0; // one partial per chunk, in item order
         b.op = OPTIGPU_OP_REDUCE;
         b.dtype = dtype;
-        b.nitems = int32_t((len + kReduceChunk - 1) / kReduceChunk);
+        b.nitems = nitems;
         b.vec_ok = (reinterpret_cast<uintptr_t>(b.src) & 15u) == 0 ? 1 : 0;
         b.th_log2 = 0;
         b.tw_log2 = 0;
-        insts[i] = b;
-        done[i] = 0u;
+        insts[k] = b;
+        done[k] = 0u;
         if (len == 0)
-            *reinterpret_cast<long long *>(out + 8 * i) = 0; // the same bits as int64 0 and double +0.0
+            *reinterpret_cast<long long *>(out + 8 * k) = 0; // the same bits as int64 0 and double +0.0
     }
-    if (i < items) {
-        int32_t lo = 0, hi = nseg - 1; // largest s with first[s] <= i and a non-empty range
-        while (lo < hi) {
-            const int32_t mid = lo + (hi - lo + 1) / 2;
-            if (first[mid] <= i)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        item_inst[i] = uint32_t(lo);
-    }
+    for (int32_t i = lane; i < nitems; i += 32)
+        item_inst[f0 + i] = uint32_t(k);
 }
 
 } // namespace
@@ -906,22 +903,30 @@ extern "C" optigpu_status optigpu_reduce_segmented(const void *src, const int64_
     }
     h_first[nseg] = it;
     char *base = static_cast<char *>(ws);
-    const int64_t *d_off = reinterpret_cast<const int64_t *>(base + off_meta);
+    // The table kernel reads the offsets straight from the pinned staging
+    // buffer when the device can address it (it always can on this part,
+    // over NVLink-C2C); otherwise they are uploaded first.  Either way the
+    // staging buffer is reused only after the event that follows its last
+    // reader.
+    const int64_t *d_off = static_cast<const int64_t *>(device_view_of_host(image, meta_bytes));
+    if (!d_off) {
+        d_off = reinterpret_cast<const int64_t *>(base + off_meta);
+        if ((st = check_cuda(cudaMemcpyAsync(base + off_meta, image, meta_bytes, cudaMemcpyHostToDevice, s),
+                             "reduce_segmented: upload offsets")) != OPTIGPU_OK)
+            return st;
+    }
     const int64_t *d_first = d_off + (nseg + 1);
-    if ((st = check_cuda(cudaMemcpyAsync(base + off_meta, image, meta_bytes, cudaMemcpyHostToDevice, s),
-                         "reduce_segmented: upload offsets")) != OPTIGPU_OK)
-        return st;
-    if ((st = check_cuda(cudaEventRecord(copied, s), "reduce_segmented: staging event")) != OPTIGPU_OK)
-        return st;
     BatchInst *d_insts = reinterpret_cast<BatchInst *>(base + L.off_inst);
     uint32_t *d_items = reinterpret_cast<uint32_t *>(base + L.off_items);
     auto *d_queue = reinterpret_cast<unsigned long long *>(base + L.off_queue);
     auto *d_done = reinterpret_cast<unsigned *>(base + L.off_done);
-    const int64_t threads = std::max<int64_t>(nseg, items);
-    seg_tables_kernel<<<unsigned((threads + 255) / 256), 256, 0, s>>>(
+    seg_tables_kernel<<<unsigned((int64_t(nseg) * 32 + 255) / 256), 256, 0, s>>>(
         static_cast<const char *>(src), int64_t(es), int(dtype), static_cast<char *>(out), d_off, d_first, nseg,
-        items, d_insts, d_items, d_queue, d_done);
-    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: tables")) != OPTIGPU_OK || items == 0)
+        d_insts, d_items, d_queue, d_done);
+    if ((st = check_cuda(cudaGetLastError(), "reduce_segmented: tables")) != OPTIGPU_OK)
+        return st;
+    if ((st = check_cuda(cudaEventRecord(copied, s), "reduce_segmented: staging event")) != OPTIGPU_OK ||
+        items == 0)
         return st;
     // The table kernel zeroed the queue and the counters (clear_done < 0).
     return batch_launch(config, d_insts, d_items, items, d_queue, d_done, -1, base + L.off_part,
