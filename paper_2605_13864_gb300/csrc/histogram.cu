@@ -38,22 +38,47 @@ struct BinRule {
 
 // The same rule in 32-bit arithmetic, valid when lo is an int32 and
 // width < 2^32: for x >= lo, x - lo lies in [0, 2^32) and is exact as an
-// unsigned 32-bit value.
+// unsigned 32-bit value.  A width that is not a power of two divides by a
+// multiply-high with a precomputed constant (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994, Fig. 4.1):
+// with l = ceil(log2 width) and m = floor(2^32 (2^l - width) / width) + 1,
+// floor(d / width) = (t + ((d - t) >> 1)) >> (l - 1), t = mulhi(m, d), for
+// every 32-bit d.
 struct BinRule32 {
     int32_t lo;
     uint32_t width;
     uint32_t nbins;
-    int shift;
+    int shift;      // log2(width) when width is a power of two, else -1
+    uint32_t magic; // m, when shift < 0
+    int l;          // ceil(log2 width), when shift < 0
 
     __device__ __forceinline__ int64_t bin(int32_t x) const
     {
         if (x < lo)
             return -1;
         const uint32_t d = uint32_t(x) - uint32_t(lo);
-        const uint32_t b = shift >= 0 ? (d >> shift) : d / width;
+        uint32_t b;
+        if (shift >= 0) {
+            b = d >> shift;
+        } else {
+            const uint32_t t = __umulhi(magic, d);
+            b = (t + ((d - t) >> 1)) >> (l - 1);
+        }
         return b < nbins ? int64_t(b) : -1;
     }
 };
+
+// Host side of BinRule32's division by a width that is not a power of two
+// (3 <= width < 2^32).
+void invariant_divisor(uint64_t width, uint32_t *magic, int *l)
+{
+    int k = 0;
+    while ((uint64_t(1) << k) < width)
+        ++k;
+    // 2^32 (2^k - width) < 2^63 since 2^k - width < width <= 2^32 and 2^k - width <= 2^31.
+    *magic = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << k) - width)) / width + 1);
+    *l = k;
+}
 
 template <bool SMEM, typename Rule>
 __global__ void __launch_bounds__(kHistThreads, 3)
@@ -165,7 +190,9 @@ extern "C" optigpu_status optigpu_histogram_i32(const int32_t *src, int64_t n, i
     auto *c = reinterpret_cast<unsigned long long *>(counts);
     const int64_t nb = nbins;
     if (narrow) {
-        const BinRule32 r32{int32_t(lo), uint32_t(width), uint32_t(nbins), rule.shift};
+        BinRule32 r32{int32_t(lo), uint32_t(width), uint32_t(nbins), rule.shift, 0u, 0};
+        if (rule.shift < 0)
+            invariant_divisor(uint64_t(width), &r32.magic, &r32.l);
         if (smem)
             histogram_kernel<true><<<unsigned(grid), kHistThreads, smem_bytes, s>>>(src, n, r32, nb, c, vec_ok);
         else

@@ -297,6 +297,17 @@ def test_histogram_matches_oracle(lo, width, nbins, n):
     assert np.array_equal(got, oracle.histogram_i32(a, lo, width, nbins))
 
 
+@pytest.mark.parametrize("width,nbins", [(3 * 2**29 + 5, 3), (1000003, 4295), (2**31 + 1, 2), (7, 1 << 20),
+                                         (3, 12288)])
+def test_histogram_full_range_widths_not_powers_of_two(width, nbins):
+    # 32-bit bins by a multiply-high with a precomputed constant: values over
+    # the whole int32 range, widths up to 2^31 + 1 (ceil(log2 width) = 32).
+    a = np.random.default_rng(width).integers(-2**31, 2**31 - 1, size=300007, dtype=np.int64).astype(np.int32)
+    a[:4] = [-2**31, 2**31 - 1, -2**31 + width - 1, -2**31 + width]
+    got = api.histogram(to_device(a, "int32"), -2**31, width, nbins).cpu().numpy()
+    assert np.array_equal(got, oracle.histogram_i32(a, -2**31, width, nbins))
+
+
 def test_histogram_unaligned_source_and_full_range():
     a = np.random.default_rng(3).integers(-2**31, 2**31 - 1, size=100003, dtype=np.int64).astype(np.int32)
     d = to_device(a, "int32", offset_elems=1)
