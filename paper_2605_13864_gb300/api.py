@@ -226,10 +226,14 @@ def tune_configs(op: str, dtype: torch.dtype = torch.float32) -> list[str]:
 
 
 def tune_select(op: str, dtype: torch.dtype, config: int) -> None:
+    """Selects the configuration ``op`` uses from now on.  The transpose
+    keeps one choice per element size; the scan one per input class (int32,
+    and the float types together); the sum and the batch kernel one each."""
     N.check(N.lib().optigpu_tune_select(_OPS[op], dtype_code(dtype), int(config)), "optigpu_tune_select")
 
 
 def tune_selected(op: str, dtype: torch.dtype) -> int:
+    """Index of the configuration ``op`` uses for ``dtype`` (see tune_select)."""
     return int(N.lib().optigpu_tune_selected(_OPS[op], dtype_code(dtype)))
 
 
