@@ -1161,13 +1161,16 @@ __device__ __forceinline__ void win_finish(const uint32_t (&raw)[WinPass<DT>::kW
         v[j] += v[j - 1];
     const uint32_t oregion = uint32_t(tid) * P::kPer * P::kOutBytes;
     if constexpr (P::kOutBytes == 4) {
+        // hi + ((lo + before) + v): the carry's low part and the thread's
+        // group prefix are added once, then each output costs two additions.
+        const float lb = sc.lo + before;
 #pragma unroll
         for (int q = 0; q < P::kPer / 4; ++q) {
             uint4 w;
-            w.x = __float_as_uint(T::finish(sc, before + v[4 * q]));
-            w.y = __float_as_uint(T::finish(sc, before + v[4 * q + 1]));
-            w.z = __float_as_uint(T::finish(sc, before + v[4 * q + 2]));
-            w.w = __float_as_uint(T::finish(sc, before + v[4 * q + 3]));
+            w.x = __float_as_uint(sc.hi + (lb + v[4 * q]));
+            w.y = __float_as_uint(sc.hi + (lb + v[4 * q + 1]));
+            w.z = __float_as_uint(sc.hi + (lb + v[4 * q + 2]));
+            w.w = __float_as_uint(sc.hi + (lb + v[4 * q + 3]));
             ptx::sts_v4(out_addr + swz128(oregion + 16u * q), w);
         }
     } else {
